@@ -1,0 +1,66 @@
+"""The Lindbladian and its matrix in the generator basis, by definition, dense (test infrastructure only).
+
+Eq. 1: L(rho) = -i[H, rho] + sum_p gamma_p ( L_p rho L_p^+ - 1/2 {L_p^+ L_p, rho} ),
+which is the paper's D_p(rho) = 1/2([L_p, rho L_p^+] + [L_p rho, L_p^+]) multiplied out.
+
+With rho = 1/N + sum_m v_m F_m (Eq. 6) and Tr(F_s F_m) = delta_sm, the unfolded
+system dv/dt = (Q + R) v + K of Eq. 8 has, by definition,
+    (Q + R)_sm = Tr(F_s L(F_m)),      K_s = Tr(F_s L(1/N)).
+This module evaluates exactly that on dense matrices (N <= ~20).
+"""
+import numpy as np
+
+from . import basis as _b
+
+
+def lindbladian(rho, H, Ls=(), gammas=()):
+    """L(rho) of Eq. 1 for dense H, dissipators Ls and rates gammas."""
+    out = -1j * (H @ rho - rho @ H)
+    for L, g in zip(Ls, gammas):
+        Ld = L.conj().T
+        LdL = Ld @ L
+        out = out + g * (L @ rho @ Ld - 0.5 * (LdL @ rho + rho @ LdL))
+    return out
+
+
+def unfold_dense(H, Ls=(), gammas=(), B=None, return_imag=False):
+    """Brute force (Q+R, K): Q_sm = Tr(F_s L(F_m)), K_s = Tr(F_s L(1/N)) (Eq. 1, 6, 8).
+
+    Returns real arrays; with ``return_imag`` also the largest imaginary part seen,
+    which must vanish because L maps Hermitian matrices to Hermitian matrices.
+    """
+    H = np.asarray(H, dtype=np.complex128)
+    N = H.shape[0]
+    if B is None:
+        B = _b.basis(N)
+    LB = np.stack([lindbladian(F, H, Ls, gammas) for F in B])
+    Q = np.einsum("sij,mji->sm", B, LB)
+    K = np.einsum("sij,ji->s", B, lindbladian(np.eye(N, dtype=np.complex128) / N, H, Ls, gammas))
+    im = max(np.abs(Q.imag).max(), np.abs(K.imag).max())
+    if return_imag:
+        return Q.real.copy(), K.real.copy(), im
+    return Q.real.copy(), K.real.copy()
+
+
+def liouvillian_vec(H, Ls=(), gammas=()):
+    """N^2 x N^2 matrix of L acting on vec(rho) (column stacking), from Eq. 1.
+
+    Uses vec(A X B) = (B^T kron A) vec(X); independent of the generator basis.
+    """
+    H = np.asarray(H, dtype=np.complex128)
+    N = H.shape[0]
+    I = np.eye(N, dtype=np.complex128)
+    S = -1j * (np.kron(I, H) - np.kron(H.T, I))
+    for L, g in zip(Ls, gammas):
+        L = np.asarray(L, dtype=np.complex128)
+        LdL = L.conj().T @ L
+        S = S + g * (np.kron(L.conj(), L) - 0.5 * np.kron(I, LdL) - 0.5 * np.kron(LdL.T, I))
+    return S
+
+
+def vec(X):
+    return np.asarray(X).reshape(-1, order="F")
+
+
+def unvec(x, N):
+    return np.asarray(x).reshape(N, N, order="F")
