@@ -1,0 +1,227 @@
+/*
+ * libgksl -- SU(N) unfolding of a GKSL master equation and RK4 propagation of the
+ * Bloch vector on one GB300 (sm_103a).  C ABI: plain pointers and sizes only.
+ *
+ * The method (arXiv:1812.11626):
+ *   Eq. 1   d rho/dt = -i[H(t), rho] + sum_p gamma_p (L_p rho L_p^+ - 1/2 {L_p^+ L_p, rho})
+ *   Eq. 6   rho = 1/N + sum_j v_j F_j over the N^2-1 traceless generators F_j of the
+ *           Sec. II list (S^(j,k), J^(j,k), D^l)
+ *   Eq. 8   dv/dt = (Q(t) + R) v + K, a real system of D = N^2-1 equations, with
+ *           Q from Eq. 7, R from Eq. 10 and K from Eq. 11
+ *   Sec. IV step 3.1: classical RK4 integration of Eq. 8.
+ * The Hamiltonian is H(t) = sum_k theta_k H0_k + eps(t) H1 with
+ * eps(t) = E + A sin(omega t), so Q(t) = Q0 + eps(t) Q1 with Q0 = sum_k theta_k Q(H0_k)
+ * + sum_p gamma_p R_p, and K = sum_p gamma_p K_p.
+ *
+ * Conventions shared by every call:
+ *  - Generator order: index s in [0, P2) is S^(j,k), j<k lexicographic, P2 = N(N-1)/2;
+ *    [P2, 2 P2) is J^(j,k) in the same order; [2 P2, D) is D^l, l = 1..N-1.  D^l is
+ *    real: (sum_{k<l} |k><k| - l |l><l|)/sqrt(l(l+1)) (the paper's list prints a
+ *    spurious factor i).  All indices are 0-based.
+ *  - N x N operator inputs are CSR with int32 row pointers (N+1) and column indices,
+ *    and separate float64 real and imaginary arrays; rows need not be sorted but an
+ *    (row, column) pair may appear only once.  Inputs are copied: the caller keeps
+ *    ownership and may free them when the call returns.
+ *  - Any pointer argument may point to host memory or to device memory of the
+ *    context's GPU; the library decides with cudaPointerGetAttributes.  Outputs are
+ *    written into caller-owned buffers of the stated size.
+ *  - Every call returns a gksl_status and never aborts; the message of the last
+ *    failure is kept per context (gksl_last_error).  A call made before the state it
+ *    needs exists (e.g. propagate before assemble) returns GKSL_ERR_STATE.
+ *  - All device work runs on the stream given to gksl_create, in stream order; calls
+ *    that return data to host memory synchronise that stream first.
+ *  - The library owns all device memory it allocates for a context and frees it in
+ *    gksl_destroy.
+ */
+#ifndef GKSL_H
+#define GKSL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GKSL_OK = 0,
+    GKSL_ERR_ARG = 1,       /* invalid argument: null pointer, size out of range, malformed CSR */
+    GKSL_ERR_CUDA = 2,      /* a CUDA runtime call failed (message in gksl_last_error) */
+    GKSL_ERR_OOM = 3,       /* a device allocation failed */
+    GKSL_ERR_STATE = 4,     /* call out of order */
+    GKSL_ERR_UNSTABLE = 5,  /* step size above the RK4 stability bound (checked runs only) */
+    GKSL_ERR_DIVERGED = 6,  /* the propagated state became non-finite */
+    GKSL_ERR_TIMEOUT = 7    /* a bounded device-side wait gave up */
+} gksl_status;
+
+typedef struct gksl_ctx gksl_ctx;
+typedef struct gksl_batch gksl_batch;
+
+#define GKSL_MAX_H0 8   /* Hamiltonian components H0_k, k < GKSL_MAX_H0 */
+#define GKSL_MAX_P 8    /* dissipative channels p < GKSL_MAX_P */
+
+/* ------------------------------------------------------------------ lifetime */
+
+/* Create a context for N x N operators (2 <= N <= 4096) on CUDA device `device`;
+ * `cuda_stream` is a cudaStream_t (NULL: the legacy default stream). */
+gksl_status gksl_create(int N, int device, void *cuda_stream, gksl_ctx **out);
+/* Free every device buffer of the context.  NULL is allowed. */
+void gksl_destroy(gksl_ctx *ctx);
+/* Message of the last failed call on this context ("" if none); valid until the next call. */
+const char *gksl_last_error(const gksl_ctx *ctx);
+
+/* ------------------------------------------------------------------ inputs (Eq. 1) */
+
+/* Hamiltonian component H0_k with weight theta_k (Eq. 1; H(t) = sum_k theta_k H0_k + eps(t) H1).
+ * Must be Hermitian; the trace part is irrelevant (Sec. II assumes H traceless).
+ * Passing nnz = 0 removes the component. */
+gksl_status gksl_set_h0_component(gksl_ctx *ctx, int k, double theta_k, const int *rowptr, const int *col,
+                                  const double *re, const double *im, int nnz);
+/* Change theta_k of an existing component without re-expanding it. */
+gksl_status gksl_set_theta(gksl_ctx *ctx, int k, double theta_k);
+/* Driven part H1 (Hermitian), multiplied by eps(t). */
+gksl_status gksl_set_h1(gksl_ctx *ctx, const int *rowptr, const int *col, const double *re, const double *im,
+                        int nnz);
+/* Dissipator L_p with rate gamma_p >= 0 (Eq. 1).  Any complex matrix; a nonzero trace part
+ * Tr(L_p)/N is folded into an effective Hamiltonian.  nnz = 0 removes the channel. */
+gksl_status gksl_set_dissipator(gksl_ctx *ctx, int p, double gamma_p, const int *rowptr, const int *col,
+                                const double *re, const double *im, int nnz);
+/* Change gamma_p of an existing channel without re-expanding it. */
+gksl_status gksl_set_gamma(gksl_ctx *ctx, int p, double gamma_p);
+/* eps(t) = E + A sin(omega t), omega > 0; the period is T = 2 pi / omega (Sec. III). */
+gksl_status gksl_set_drive(gksl_ctx *ctx, double E, double A, double omega);
+
+/* ------------------------------------------------------------------ expansion (Sec. IV step 2.1) */
+
+/* Coefficients x_s = Tr(F_s X), s < D, of an N x N CSR matrix X (host or device arrays).
+ * coef_re/coef_im: D doubles each (coef_im may be NULL). */
+gksl_status gksl_expand(gksl_ctx *ctx, const int *rowptr, const int *col, const double *re, const double *im,
+                        int nnz, double *coef_re, double *coef_im);
+
+/* ------------------------------------------------------------------ structure constants (Eq. 5) */
+
+#define GKSL_STRUCT_F 0   /* f_mns = -i Tr(F_s [F_m, F_n]) */
+#define GKSL_STRUCT_D 1   /* d_mns = Tr(F_s {F_m, F_n}) */
+
+/* Number of nonzero ordered triples (m, n, s) of f or d for dimension N, counted on the device
+ * by enumerating the closed-form nonzero set (Sec. IV step 2.2 gives 5N^3-9N^2-2N+6 and
+ * 6N^3-N(21N+7)/2+1).  Uses the current device; allocates a few bytes. */
+gksl_status gksl_structure_count(int N, int which, long long *count);
+/* Every nonzero (m, n, s, value) of f or d, written to caller buffers of `capacity` entries
+ * (host or device).  *count receives the total; if it exceeds capacity nothing is written and
+ * GKSL_ERR_ARG is returned. */
+gksl_status gksl_structure_enumerate(int N, int which, long long capacity, int *m, int *n, int *s,
+                                     double *value, long long *count);
+
+/* ------------------------------------------------------------------ assembly (Sec. IV steps 2.1-2.5) */
+
+#define GKSL_ASM_FP32 1u        /* also build the FP32 copies used by precision 32 */
+#define GKSL_ASM_TRANSPOSE 2u   /* also build the transposes used by the adjoint */
+#define GKSL_ASM_NO_DROP 4u     /* keep entries |q| <= 64 eps max|Q| in Q0 */
+
+/* Build Q(H0_k), Q(H1), R_p, K_p on the device from the structure constants (Eq. 7, 10, 11),
+ * then Q0, Q1 and K.  `seconds` (may be NULL) receives the wall time of the call. */
+gksl_status gksl_assemble(gksl_ctx *ctx, unsigned flags, double *seconds);
+
+#define GKSL_MAT_Q0 0      /* sum_k theta_k Q(H0_k) + sum_p gamma_p R_p (no eps term) */
+#define GKSL_MAT_Q1 1      /* Q(H1) */
+#define GKSL_MAT_H0 16     /* + k: Q(H0_k) alone (Eq. 7) */
+#define GKSL_MAT_R 32      /* + p: R_p at unit rate (Eq. 10), including the trace-part Hamiltonian */
+
+/* Copy one assembled D x D matrix as CSR (rows sorted by column) into caller buffers:
+ * rowptr (D+1 int32), col (nnz int32), val (nnz float64).  With rowptr == NULL only *nnz is set. */
+gksl_status gksl_get_csr(gksl_ctx *ctx, int which, long long *nnz, int *rowptr, int *col, double *val);
+/* K = sum_p gamma_p K_p (Eq. 11), D doubles. */
+gksl_status gksl_get_k(gksl_ctx *ctx, double *K);
+/* K_p at unit rate, D doubles. */
+gksl_status gksl_get_k_channel(gksl_ctx *ctx, int p, double *K);
+
+/* ------------------------------------------------------------------ state (Eq. 6) */
+
+/* v(0) = Tr(F_j rho0) from a dense N x N rho0 (row-major re and im, im may be NULL); t = 0
+ * (Sec. IV step 2.6). */
+gksl_status gksl_set_rho0(gksl_ctx *ctx, const double *re, const double *im);
+gksl_status gksl_set_state(gksl_ctx *ctx, const double *v, double t);
+gksl_status gksl_get_state(gksl_ctx *ctx, double *v, double *t);
+
+/* ------------------------------------------------------------------ propagation (Sec. IV step 3.1) */
+
+/* Smallest steps per period for which h * (Gershgorin bound of ||Q(t)||) <= 2.6 for all t
+ * (RK4 is stable on the imaginary axis up to 2 sqrt 2).  Needs gksl_assemble. */
+gksl_status gksl_min_stable_steps(gksl_ctx *ctx, long long *steps_per_period);
+
+/* Advance the state by n_steps classical RK4 steps of h = T / steps_per_period from the
+ * current (v, t).  precision 64: FP64 throughout.  precision 32: FP32 matrix, stage vectors
+ * and arithmetic, FP64 master state (the FP32 increment is added to it every step) and,
+ * every `correction_every` steps (<= 0: never), one full FP64 step in place of an FP32 one.
+ * Every `emit_every` steps (<= 0: never) the FP64 state is copied to v_out, which holds
+ * (n_steps / emit_every) rows of D doubles.  Returns GKSL_ERR_DIVERGED if the state is
+ * non-finite at an emission point or at the end. */
+gksl_status gksl_propagate(gksl_ctx *ctx, long long steps_per_period, long long n_steps, int precision,
+                           long long correction_every, long long emit_every, double *v_out);
+
+/* ------------------------------------------------------------------ observables (Eq. 6) */
+
+/* <O> = Tr(O)/N + sum_j v_j Tr(O F_j) for a diagonal O (o_diag: N doubles) and `count` state
+ * vectors stored back to back in v (count x D doubles); out: count doubles. */
+gksl_status gksl_observable_diag(gksl_ctx *ctx, const double *o_diag, const double *v, long long count,
+                                 double *out);
+/* Dense rho = 1/N + sum_j v_j F_j (Eq. 6), row-major N x N re and im. */
+gksl_status gksl_rho(gksl_ctx *ctx, const double *v, double *re, double *im);
+
+/* ------------------------------------------------------------------ adjoint */
+
+/* Loss = trapezoid mean of <O> over the steps_per_period+1 grid points of period
+ * `period_index` (1-based) of an RK4 run from the current state, and its exact gradient by
+ * the discrete adjoint of the RK4 map (per-period checkpoints, recomputation in between).
+ * grad receives n_grad doubles in the order [d/dA, d/dgamma_0 .. d/dgamma_{P-1},
+ * d/dtheta_0 .. d/dtheta_{K-1}] over the set channels and components in index order.
+ * Requires gksl_assemble with GKSL_ASM_TRANSPOSE.  The state is left unchanged. */
+gksl_status gksl_adjoint_timeavg(gksl_ctx *ctx, const double *o_diag, long long steps_per_period,
+                                 long long period_index, int precision, double *loss, double *grad, int n_grad);
+
+/* ------------------------------------------------------------------ batched instances */
+
+/* A batch of instances that share the unfolded components of an assembled context per
+ * group and differ in the drive amplitude A_b and a dissipation scale g_b:
+ *   dv_b/dt = (Q0_H + eps_b(t) Q1 + g_b R) v_b + g_b K,  eps_b(t) = E + A_b sin(omega t),
+ * where Q0_H = sum_k theta_k Q(H0_k) and R, K are the context's gamma-weighted dissipator
+ * terms.  groups[i] must stay alive while the batch exists.  A and g hold one value per
+ * instance, group by group (n_inst[0] values of group 0 first). */
+gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, const int *n_inst, const double *A,
+                              const double *g, gksl_batch **out);
+void gksl_batch_destroy(gksl_batch *b);
+const char *gksl_batch_last_error(const gksl_batch *b);
+/* Reset every instance to its group's current state vector, t = 0. */
+gksl_status gksl_batch_reset(gksl_batch *b);
+/* Advance every group by `periods` periods of steps_per_period[i] steps (FP32 bulk, FP64 master
+ * state, an FP64 step every correction_every steps, <= 0: never).  `seconds` (may be NULL)
+ * receives the device time of the whole run. */
+gksl_status gksl_batch_propagate(gksl_batch *b, const long long *steps_per_period, long long periods,
+                                 long long correction_every, double *seconds);
+/* State of instance i (D_i doubles, FP64 master). */
+gksl_status gksl_batch_get_state(gksl_batch *b, int instance, double *v);
+/* Tile width chosen by the autotuner for group `group` (instances per lane; one warp covers
+ * 32 * instances_per_lane instances of a row) and its timed cost per FP32 step in microseconds.
+ * Both are 0 before the first gksl_batch_propagate. */
+gksl_status gksl_batch_info(gksl_batch *b, int group, int *instances_per_lane, double *tuned_us_per_step);
+
+/* ------------------------------------------------------------------ introspection */
+
+typedef struct {
+    int N;
+    long long D;
+    long long nnz_q0;          /* propagation matrix Q0 + E Q1 after the drop */
+    long long nnz_q1;
+    long long nnz_r[GKSL_MAX_P];
+    int ell_width_q0;          /* ELL slots per row of the propagation format */
+    int ell_width_q1;
+    long long long_rows;       /* rows handled warp-per-row */
+    long long device_bytes;    /* device memory held by the context */
+    double assemble_seconds;
+    double max_abs_q0;
+} gksl_info;
+
+gksl_status gksl_get_info(gksl_ctx *ctx, gksl_info *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GKSL_H */

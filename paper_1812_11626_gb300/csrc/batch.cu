@@ -1,0 +1,611 @@
+// Batched propagation: many instances of Eq. 8 that share the unfolded components and differ
+// in the drive amplitude A_b and a dissipation scale g_b,
+//     dv_b/dt = (QH + A_b sin(omega t) Q1 + g_b R) v_b + g_b K,
+// with QH = sum_k theta_k Q(H0_k) + E Q1 and R, K the gamma-weighted dissipator terms of a
+// group's context.  The state of a group is a (D+1) x B matrix V (instance index fastest,
+// row D = 1 so that K rides as an extra column of R), and every RK4 stage is a sparse-matrix
+// times dense-matrix product with three value channels.
+//
+// One persistent launch per stage covers every group (mixed N): each CTA walks the tile list
+// (group, 8-row block, instance chunk); a warp owns one row and its 32 lanes own consecutive
+// instances, so each matrix entry is loaded once per chunk and the gathers V[col, b] are
+// coalesced.  Chunks are 32 * ipl instances wide (ipl instances per lane), chosen per group by
+// timing the candidates (autotuner).  Groups with fewer steps drop out of the tile walk when
+// they finish.  The FP32 bulk updates an FP64 master state every step; every
+// `correction_every` steps one FP64 step replaces an FP32 one.  Chunks of steps are captured
+// in CUDA graphs.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "prim.cuh"
+
+namespace gk {
+namespace {
+
+constexpr int kBThreads = 256;
+constexpr int kRowsPerTile = kBThreads / 32;
+constexpr int kMaxIpl = 4;
+constexpr int kMaxGroups = 8;
+constexpr int kBatchGraphSteps = 32;
+
+struct GroupDev {
+    const int *ptr[3];
+    const int *col[3];
+    const float *vf[3];
+    const double *vd[3];
+    long long D;
+    int B, ipl, nchunks;
+    long long nsteps;
+    double h;
+    const double *sin_tab;   // sin(omega t) at the 3 stage times of each step
+    const double *A, *g;
+    double *V64;
+    float *V32, *Y32[2], *ACC32;
+    double *Y64[2], *ACC64;
+    long long tile_begin, ntiles;
+};
+
+struct BatchArgs {
+    GroupDev gr[kMaxGroups];
+    int ng;
+    long long ntiles;
+    const long long *base;
+    long long local;
+};
+
+template <int STAGE, bool F64>
+__global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
+    const long long step = *a.base + a.local;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        int gi = 0;
+        while (gi + 1 < a.ng && t >= a.gr[gi + 1].tile_begin) ++gi;
+        const GroupDev &G = a.gr[gi];
+        if (step >= G.nsteps) continue;
+        long long tl = t - G.tile_begin;
+        long long r = (tl / G.nchunks) * kRowsPerTile + warp;
+        int ch = (int)(tl % G.nchunks);
+        if (r >= G.D) continue;
+        const int B = G.B;
+        using VT = typename std::conditional<F64, double, float>::type;
+        const VT *X;
+        if (F64) X = (const VT *)(STAGE == 1 ? G.V64 : (STAGE == 3 ? G.Y64[1] : G.Y64[0]));
+        else X = (const VT *)(STAGE == 1 ? (void *)G.V32 : (STAGE == 3 ? (void *)G.Y32[1] : (void *)G.Y32[0]));
+        VT acc[3][kMaxIpl];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k = 0; k < kMaxIpl; ++k) acc[c][k] = VT(0);
+        const int b0 = ch * 32 * G.ipl + lane;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int e1 = G.ptr[c][r + 1];
+            for (int e = G.ptr[c][r]; e < e1; ++e) {
+                const int col = G.col[c][e];
+                const VT v = F64 ? (VT)G.vd[c][e] : (VT)G.vf[c][e];
+                const VT *xr = X + (long long)col * B;
+#pragma unroll
+                for (int k = 0; k < kMaxIpl; ++k) {
+                    int b = b0 + 32 * k;
+                    if (k < G.ipl && b < B) acc[c][k] += v * __ldg(xr + b);
+                }
+            }
+        }
+        const int slot = STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1);
+        const double sn = G.sin_tab[3 * step + slot];
+        const double h = G.h;
+#pragma unroll
+        for (int k = 0; k < kMaxIpl; ++k) {
+            int b = b0 + 32 * k;
+            if (k >= G.ipl || b >= B) continue;
+            long long o = r * B + b;
+            VT kv = acc[0][k] + (VT)(G.A[b] * sn) * acc[1][k] + (VT)G.g[b] * acc[2][k];
+            if (F64) {
+                double *yn = STAGE == 1 ? G.Y64[0] : (STAGE == 2 ? G.Y64[1] : G.Y64[0]);
+                double kd = (double)kv;
+                if (STAGE == 1) { yn[o] = G.V64[o] + (0.5 * h) * kd; G.ACC64[o] = kd; }
+                if (STAGE == 2) { yn[o] = G.V64[o] + (0.5 * h) * kd; G.ACC64[o] += 2.0 * kd; }
+                if (STAGE == 3) { yn[o] = G.V64[o] + h * kd; G.ACC64[o] += 2.0 * kd; }
+                if (STAGE == 4) { G.V64[o] = G.V64[o] + (h / 6.0) * (G.ACC64[o] + kd); G.V32[o] = (float)G.V64[o]; }
+            } else {
+                float *yn = STAGE == 1 ? G.Y32[0] : (STAGE == 2 ? G.Y32[1] : G.Y32[0]);
+                float kf = (float)kv, hf = (float)h;
+                if (STAGE == 1) { yn[o] = G.V32[o] + (0.5f * hf) * kf; G.ACC32[o] = kf; }
+                if (STAGE == 2) { yn[o] = G.V32[o] + (0.5f * hf) * kf; G.ACC32[o] += 2.0f * kf; }
+                if (STAGE == 3) { yn[o] = G.V32[o] + hf * kf; G.ACC32[o] += 2.0f * kf; }
+                if (STAGE == 4) {
+                    float inc = (float)(h / 6.0) * (G.ACC32[o] + kf);
+                    double nv = G.V64[o] + (double)inc;
+                    G.V64[o] = nv;
+                    G.V32[o] = (float)nv;
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_sin_table(double t0, double h, double omega, long long n, double *__restrict__ tab) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double tn = t0 + (double)i * h;
+    tab[3 * i + 0] = sin(omega * tn);
+    tab[3 * i + 1] = sin(omega * (tn + 0.5 * h));
+    tab[3 * i + 2] = sin(omega * (tn + h));
+}
+
+__global__ void k_replicate(const double *__restrict__ v, long long rows, int B, double *__restrict__ V64,
+                            float *__restrict__ V32) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * B) return;
+    double x = v[i / B];
+    V64[i] = x;
+    V32[i] = (float)x;
+}
+
+__global__ void k_fill_row(double *V64, float *V32, float *Ya, float *Yb, double *Y64a, double *Y64b, long long row,
+                           int B) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    long long o = row * B + b;
+    V64[o] = 1.0;
+    V32[o] = 1.0f;
+    Ya[o] = 1.0f;
+    Yb[o] = 1.0f;
+    Y64a[o] = 1.0;
+    Y64b[o] = 1.0;
+}
+
+__global__ void k_column(const double *__restrict__ V, long long rows, int B, int b, double *__restrict__ out) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < rows) out[r] = V[r * B + b];
+}
+
+__global__ void k_to_f32b(const double *__restrict__ v, float *__restrict__ o, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) o[i] = (float)v[i];
+}
+
+__global__ void k_set_base(long long *p, long long v) { *p = v; }
+
+struct Group {
+    gksl_ctx *ctx = nullptr;
+    long long D = 0;
+    int B = 0;
+    int ipl = 1;
+    CsrR m[3];            // QH (E folded), Q1, [R | K]
+    DBuf<float> mf[3];    // FP32 values
+    DBuf<double> A, g, V64, Y64a, Y64b, ACC64, sin_tab;
+    DBuf<float> V32, Ya, Yb, ACC32;
+    long long nsteps = 0;
+    double h = 0.0;
+    double tuned_us = 0.0;
+};
+
+}  // namespace
+}  // namespace gk
+
+struct gksl_batch {
+    std::vector<gk::Group> groups;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    gk::DBuf<long long> base;
+    std::vector<int> first_instance;   // global instance index of each group's first instance
+    int n_instances = 0;
+    struct Graph {
+        int f64;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    bool tuned = false;
+    ~gksl_batch() {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace gk {
+namespace {
+
+__global__ void k_f2(const double *__restrict__ v, float *__restrict__ o, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) o[i] = (float)v[i];
+}
+
+BatchArgs make_args(gksl_batch *b, long long local) {
+    BatchArgs a{};
+    a.ng = (int)b->groups.size();
+    long long tb = 0;
+    for (int i = 0; i < a.ng; ++i) {
+        Group &G = b->groups[i];
+        GroupDev &d = a.gr[i];
+        for (int c = 0; c < 3; ++c) {
+            d.ptr[c] = G.m[c].rowptr.p;
+            d.col[c] = G.m[c].col.p;
+            d.vf[c] = G.mf[c].p;
+            d.vd[c] = G.m[c].val.p;
+        }
+        d.D = G.D;
+        d.B = G.B;
+        d.ipl = G.ipl;
+        d.nchunks = (G.B + 32 * G.ipl - 1) / (32 * G.ipl);
+        d.nsteps = G.nsteps;
+        d.h = G.h;
+        d.sin_tab = G.sin_tab.p;
+        d.A = G.A.p;
+        d.g = G.g.p;
+        d.V64 = G.V64.p;
+        d.V32 = G.V32.p;
+        d.Y32[0] = G.Ya.p;
+        d.Y32[1] = G.Yb.p;
+        d.ACC32 = G.ACC32.p;
+        d.Y64[0] = G.Y64a.p;
+        d.Y64[1] = G.Y64b.p;
+        d.ACC64 = G.ACC64.p;
+        d.tile_begin = tb;
+        d.ntiles = ((G.D + kRowsPerTile - 1) / kRowsPerTile) * d.nchunks;
+        tb += d.ntiles;
+    }
+    a.ntiles = tb;
+    a.base = b->base.p;
+    a.local = local;
+    return a;
+}
+
+unsigned batch_grid(long long ntiles) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long g = (long long)sms * 8;
+    if (g > ntiles) g = ntiles;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+void launch_batch_step(gksl_batch *b, bool f64, long long local) {
+    BatchArgs a = make_args(b, local);
+    unsigned grid = batch_grid(a.ntiles);
+    cudaStream_t s = b->stream;
+    if (f64) {
+        k_batch_stage<1, true><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<2, true><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<3, true><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<4, true><<<grid, kBThreads, 0, s>>>(a);
+    } else {
+        k_batch_stage<1, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<2, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<3, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<4, false><<<grid, kBThreads, 0, s>>>(a);
+    }
+    GK_LAUNCH_CHECK();
+}
+
+void clear_batch_graphs(gksl_batch *b) {
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+}
+
+cudaGraphExec_t batch_graph(gksl_batch *b, bool f64) {
+    for (auto &g : b->graphs)
+        if (g.f64 == (int)f64) return g.exec;
+    cudaGraph_t graph;
+    GK_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < kBatchGraphSteps; ++i) launch_batch_step(b, f64, i);
+    GK_CUDA(cudaStreamEndCapture(b->stream, &graph));
+    cudaGraphExec_t exec;
+    GK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    GK_CUDA(cudaGraphDestroy(graph));
+    b->graphs.push_back({(int)f64, exec});
+    return exec;
+}
+
+void run_batch_steps(gksl_batch *b, bool f64, long long first, long long count) {
+    long long n = first, end = first + count;
+    while (end - n >= kBatchGraphSteps) {
+        k_set_base<<<1, 1, 0, b->stream>>>(b->base.p, n);
+        GK_LAUNCH_CHECK();
+        GK_CUDA(cudaGraphLaunch(batch_graph(b, f64), b->stream));
+        n += kBatchGraphSteps;
+    }
+    if (n < end) {
+        k_set_base<<<1, 1, 0, b->stream>>>(b->base.p, n);
+        GK_LAUNCH_CHECK();
+        for (long long i = 0; n + i < end; ++i) launch_batch_step(b, f64, i);
+    }
+}
+
+void reset_batch(gksl_batch *b) {
+    for (auto &G : b->groups) {
+        gksl_ctx *c = G.ctx;
+        GK_REQUIRE(c->state_set, GKSL_ERR_STATE, "a group context has no state");
+        long long rows = G.D + 1;
+        k_replicate<<<grid_for(rows * G.B, 256), 256, 0, b->stream>>>(c->v.p, rows, G.B, G.V64.p, G.V32.p);
+        GK_LAUNCH_CHECK();
+        k_fill_row<<<grid_for(G.B, 128), 128, 0, b->stream>>>(G.V64.p, G.V32.p, G.Ya.p, G.Yb.p, G.Y64a.p, G.Y64b.p,
+                                                               G.D, G.B);
+        GK_LAUNCH_CHECK();
+    }
+    GK_CUDA(cudaStreamSynchronize(b->stream));
+}
+
+// Time every candidate chunk width on a few FP32 steps of the group alone; keep the fastest.
+void autotune(gksl_batch *b) {
+    std::vector<Group *> all;
+    for (auto &G : b->groups) all.push_back(&G);
+    cudaEvent_t e0, e1;
+    GK_CUDA(cudaEventCreate(&e0));
+    GK_CUDA(cudaEventCreate(&e1));
+    for (auto *G : all) {
+        // run this group alone: other groups get nsteps = 0 for the trial
+        std::vector<long long> saved;
+        for (auto *H : all) saved.push_back(H->nsteps);
+        for (auto *H : all) H->nsteps = (H == G) ? 1LL << 40 : 0;
+        std::vector<double> tab_saved;
+        if (G->sin_tab.n < 3 * 64) G->sin_tab.alloc(3 * 64);
+        k_sin_table<<<1, 64, 0, b->stream>>>(0.0, 1e-6, 1.0, 16, G->sin_tab.p);
+        GK_LAUNCH_CHECK();
+        double best = 1e300;
+        int best_ipl = 1;
+        for (int ipl = 1; ipl <= kMaxIpl; ++ipl) {
+            if (32 * (ipl - 1) >= G->B) break;   // wider chunks than the batch add nothing
+            G->ipl = ipl;
+            G->h = 1e-6;   // tiny step: the trial leaves the state essentially unchanged
+            k_set_base<<<1, 1, 0, b->stream>>>(b->base.p, 0);
+            for (int w = 0; w < 2; ++w) launch_batch_step(b, false, w);
+            GK_CUDA(cudaEventRecord(e0, b->stream));
+            for (int w = 0; w < 8; ++w) launch_batch_step(b, false, w);
+            GK_CUDA(cudaEventRecord(e1, b->stream));
+            GK_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; best_ipl = ipl; }
+        }
+        G->ipl = best_ipl;
+        G->tuned_us = best * 1000.0 / 8.0;
+        for (size_t i = 0; i < all.size(); ++i) all[i]->nsteps = saved[i];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    reset_batch(b);   // the trials touched the states
+    clear_batch_graphs(b);
+    b->tuned = true;
+}
+
+}  // namespace
+}  // namespace gk
+
+using namespace gk;
+
+namespace {
+template <typename F>
+gksl_status bguarded(gksl_batch *b, F &&f) {
+    if (!b) return GKSL_ERR_ARG;
+    try {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (prev != b->device) cudaSetDevice(b->device);
+        b->err.clear();
+        f();
+        return GKSL_OK;
+    } catch (const Error &e) {
+        b->err = e.msg;
+        return e.st;
+    } catch (const std::exception &e) {
+        b->err = e.what();
+        return GKSL_ERR_ARG;
+    }
+}
+}  // namespace
+
+extern "C" gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, const int *n_inst, const double *A,
+                                         const double *g, gksl_batch **out) {
+    if (!out || n_groups < 1 || n_groups > kMaxGroups || !groups || !n_inst || !A || !g) return GKSL_ERR_ARG;
+    *out = nullptr;
+    gksl_batch *b = new (std::nothrow) gksl_batch();
+    if (!b) return GKSL_ERR_OOM;
+    b->device = groups[0] ? groups[0]->device : 0;
+    gksl_status st = bguarded(b, [&] {
+        GK_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->base.alloc(1);
+        int total = 0;
+        for (int i = 0; i < n_groups; ++i) {
+            GK_REQUIRE(groups[i] && n_inst[i] > 0, GKSL_ERR_ARG, "every group needs a context and >= 1 instance");
+            GK_REQUIRE(groups[i]->assembled, GKSL_ERR_STATE, "group contexts must be assembled");
+            GK_REQUIRE(groups[i]->device == b->device, GKSL_ERR_ARG, "all groups must live on one device");
+            total += n_inst[i];
+        }
+        std::vector<double> hA(A, A + total), hg(g, g + total);
+        for (int i = 0; i < total; ++i)
+            GK_REQUIRE(std::isfinite(hA[i]) && std::isfinite(hg[i]) && hg[i] >= 0.0, GKSL_ERR_ARG,
+                       "instance parameters must be finite with g >= 0");
+        b->groups.resize((size_t)n_groups);
+        int off = 0;
+        for (int i = 0; i < n_groups; ++i) {
+            gksl_ctx *c = groups[i];
+            Group &G = b->groups[i];
+            G.ctx = c;
+            G.D = c->D;
+            G.B = n_inst[i];
+            b->first_instance.push_back(off);
+            cudaStream_t s = c->stream;
+            // channels from the group's components: QH = sum theta Q(H0_k) + E Q1, Q1, [R | K]
+            std::vector<std::pair<const CsrR *, double>> th, rr;
+            for (int k = 0; k < GKSL_MAX_H0; ++k)
+                if (c->has_h0[k]) th.push_back({&c->QH0[k], c->h0[k].weight});
+            th.push_back({&c->Q1, c->E});
+            for (int p = 0; p < GKSL_MAX_P; ++p)
+                if (c->has_r[p]) rr.push_back({&c->R[p], c->diss[p].weight});
+            // merge through COO (same reduction as the assembly, no drop)
+            auto build = [&](const std::vector<std::pair<const CsrR *, double>> &terms, const double *kcol, CsrR &out) {
+                long long n = kcol ? c->D : 0;
+                for (auto &t : terms) n += t.first->nnz;
+                std::vector<uint64_t> hk;
+                std::vector<double> hv;
+                hk.reserve((size_t)n);
+                hv.reserve((size_t)n);
+                long long ncols = kcol ? c->D + 1 : c->D;
+                for (auto &t : terms) {
+                    std::vector<int> rp((size_t)c->D + 1), cc((size_t)std::max(1LL, t.first->nnz));
+                    std::vector<double> vv((size_t)std::max(1LL, t.first->nnz));
+                    GK_CUDA(cudaMemcpyAsync(rp.data(), t.first->rowptr.p, sizeof(int) * (c->D + 1),
+                                            cudaMemcpyDeviceToHost, s));
+                    if (t.first->nnz > 0) {
+                        GK_CUDA(cudaMemcpyAsync(cc.data(), t.first->col.p, sizeof(int) * t.first->nnz,
+                                                cudaMemcpyDeviceToHost, s));
+                        GK_CUDA(cudaMemcpyAsync(vv.data(), t.first->val.p, sizeof(double) * t.first->nnz,
+                                                cudaMemcpyDeviceToHost, s));
+                    }
+                    GK_CUDA(cudaStreamSynchronize(s));
+                    for (long long r = 0; r < c->D; ++r)
+                        for (int e = rp[r]; e < rp[r + 1]; ++e) {
+                            hk.push_back((uint64_t)r * (uint64_t)ncols + (uint64_t)cc[e]);
+                            hv.push_back(t.second * vv[e]);
+                        }
+                }
+                if (kcol) {
+                    std::vector<double> kk((size_t)c->D);
+                    GK_CUDA(cudaMemcpyAsync(kk.data(), kcol, sizeof(double) * c->D, cudaMemcpyDeviceToHost, s));
+                    GK_CUDA(cudaStreamSynchronize(s));
+                    for (long long r = 0; r < c->D; ++r)
+                        if (kk[r] != 0.0) {
+                            hk.push_back((uint64_t)r * (uint64_t)ncols + (uint64_t)c->D);
+                            hv.push_back(kk[r]);
+                        }
+                }
+                long long m = (long long)hk.size();
+                DBuf<uint64_t> dk((size_t)std::max(1LL, m));
+                DBuf<double> dv((size_t)std::max(1LL, m));
+                if (m > 0) {
+                    GK_CUDA(cudaMemcpyAsync(dk.p, hk.data(), sizeof(uint64_t) * m, cudaMemcpyHostToDevice, s));
+                    GK_CUDA(cudaMemcpyAsync(dv.p, hv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+                }
+                GK_CUDA(cudaStreamSynchronize(s));
+                coo_to_csr_real(dk, dv, m, c->D, ncols, 0.0, out, s);
+            };
+            build(th, nullptr, G.m[0]);
+            build({{&c->Q1, 1.0}}, nullptr, G.m[1]);
+            build(rr, c->K.p, G.m[2]);
+            for (int ch = 0; ch < 3; ++ch) {
+                G.mf[ch].alloc((size_t)std::max(1LL, G.m[ch].nnz));
+                if (G.m[ch].nnz > 0) {
+                    k_f2<<<grid_for(G.m[ch].nnz, 256), 256, 0, s>>>(G.m[ch].val.p, G.mf[ch].p, G.m[ch].nnz);
+                    GK_LAUNCH_CHECK();
+                }
+            }
+            GK_CUDA(cudaStreamSynchronize(s));
+            G.A.alloc((size_t)G.B);
+            G.g.alloc((size_t)G.B);
+            GK_CUDA(cudaMemcpy(G.A.p, hA.data() + off, sizeof(double) * G.B, cudaMemcpyHostToDevice));
+            GK_CUDA(cudaMemcpy(G.g.p, hg.data() + off, sizeof(double) * G.B, cudaMemcpyHostToDevice));
+            long long n = (G.D + 1) * G.B;
+            G.V64.alloc((size_t)n);
+            G.Y64a.alloc((size_t)n);
+            G.Y64b.alloc((size_t)n);
+            G.ACC64.alloc((size_t)n);
+            G.V32.alloc((size_t)n);
+            G.Ya.alloc((size_t)n);
+            G.Yb.alloc((size_t)n);
+            G.ACC32.alloc((size_t)n);
+            off += G.B;
+        }
+        b->n_instances = total;
+        reset_batch(b);
+    });
+    if (st != GKSL_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return GKSL_OK;
+}
+
+extern "C" void gksl_batch_destroy(gksl_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    delete b;
+}
+
+extern "C" const char *gksl_batch_last_error(const gksl_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" gksl_status gksl_batch_reset(gksl_batch *b) {
+    return bguarded(b, [&] { reset_batch(b); });
+}
+
+extern "C" gksl_status gksl_batch_propagate(gksl_batch *b, const long long *spp, long long periods,
+                                            long long correction_every, double *seconds) {
+    return bguarded(b, [&] {
+        GK_REQUIRE(spp && periods >= 0, GKSL_ERR_ARG, "steps_per_period array required, periods >= 0");
+        if (!b->tuned) autotune(b);
+        long long maxsteps = 0;
+        for (size_t i = 0; i < b->groups.size(); ++i) {
+            Group &G = b->groups[i];
+            GK_REQUIRE(spp[i] > 0, GKSL_ERR_ARG, "steps_per_period must be > 0");
+            double T = 2.0 * M_PI / G.ctx->omega;
+            double h = T / (double)spp[i];
+            long long n = spp[i] * periods;
+            if (G.h != h || G.nsteps != n) clear_batch_graphs(b);
+            G.h = h;
+            G.nsteps = n;
+            if (G.sin_tab.n < (size_t)(3 * std::max(1LL, n))) {
+                G.sin_tab.alloc((size_t)(3 * std::max(1LL, n)));
+                clear_batch_graphs(b);
+            }
+            if (n > 0) {
+                k_sin_table<<<grid_for(n, 256), 256, 0, b->stream>>>(0.0, h, G.ctx->omega, n, G.sin_tab.p);
+                GK_LAUNCH_CHECK();
+            }
+            maxsteps = std::max(maxsteps, n);
+        }
+        cudaEvent_t e0, e1;
+        GK_CUDA(cudaEventCreate(&e0));
+        GK_CUDA(cudaEventCreate(&e1));
+        GK_CUDA(cudaEventRecord(e0, b->stream));
+        long long n = 0;
+        while (n < maxsteps) {
+            long long stop = maxsteps;
+            long long corr = -1;
+            if (correction_every > 0) corr = (n / correction_every + 1) * correction_every - 1;
+            if (corr >= 0 && corr < stop) {
+                if (corr > n) run_batch_steps(b, false, n, corr - n);
+                run_batch_steps(b, true, corr, 1);
+                n = corr + 1;
+            } else {
+                run_batch_steps(b, false, n, stop - n);
+                n = stop;
+            }
+        }
+        GK_CUDA(cudaEventRecord(e1, b->stream));
+        GK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (seconds) *seconds = ms * 1e-3;
+    });
+}
+
+extern "C" gksl_status gksl_batch_get_state(gksl_batch *b, int instance, double *v) {
+    return bguarded(b, [&] {
+        GK_REQUIRE(v && instance >= 0 && instance < b->n_instances, GKSL_ERR_ARG, "bad instance or null v");
+        size_t gi = 0;
+        while (gi + 1 < b->groups.size() && instance >= b->first_instance[gi + 1]) ++gi;
+        Group &G = b->groups[gi];
+        DBuf<double> col((size_t)G.D);
+        k_column<<<grid_for(G.D, 256), 256, 0, b->stream>>>(G.V64.p, G.D, G.B, instance - b->first_instance[gi],
+                                                            col.p);
+        GK_LAUNCH_CHECK();
+        copy_out(v, col.p, sizeof(double) * G.D, b->stream);
+        GK_CUDA(cudaStreamSynchronize(b->stream));
+    });
+}
+
+extern "C" gksl_status gksl_batch_info(gksl_batch *b, int group, int *instances_per_lane, double *tuned_us_per_step) {
+    return bguarded(b, [&] {
+        GK_REQUIRE(group >= 0 && group < (int)b->groups.size(), GKSL_ERR_ARG, "bad group");
+        if (instances_per_lane) *instances_per_lane = b->groups[group].ipl;
+        if (tuned_us_per_step) *tuned_us_per_step = b->groups[group].tuned_us;
+    });
+}

@@ -1,0 +1,61 @@
+// Cross-file entry points of the library (inside namespace gk).
+#pragma once
+
+#include "common.cuh"
+
+namespace gk {
+
+// ---- expand.cu (Sec. IV steps 2.1 and 2.6, Eq. 6)
+// Dense coefficient vector Tr(F_s X), s < D, of an input operator (complex, D entries).
+void expand_op(gksl_ctx *c, const Op &op, DBuf<double2> &coef);
+// v = Re Tr(F_s rho) of a dense device matrix (re, im may be null), written to v_dev (D entries).
+void expand_dense(gksl_ctx *c, const double *re_dev, const double *im_dev, double *v_dev);
+// <O> for count vectors (device) -> out_dev
+void observable_diag(gksl_ctx *c, const double *o_diag_dev, const double *v_dev, long long count, long long ldv,
+                     double *out_dev);
+void rho_dense(gksl_ctx *c, const double *v_dev, double *re_dev, double *im_dev);
+// observable weights w_l = Tr(O D^l) into a dense length-D vector (zeros off the D block) and c0
+void observable_weights(gksl_ctx *c, const double *o_diag_dev, double *w_dev, double *c0_dev);
+// <O> = c0 + w.v for count vectors with weights from observable_weights (no synchronisation)
+void observable_apply(gksl_ctx *c, const double *w, const double *c0, const double *v, long long count, long long ldv,
+                      double *out);
+
+// ---- assemble.cu (Sec. IV steps 2.2-2.5)
+void assemble(gksl_ctx *c, unsigned flags);
+
+// ---- rk4.cu (Sec. IV step 3.1)
+void propagate(gksl_ctx *c, long long spp, long long n_steps, int precision, long long corr_every,
+               long long emit_every, double *v_out, bool out_on_device);
+void ensure_work(gksl_ctx *c, bool fp32);
+void clear_graphs(gksl_ctx *c);
+bool state_finite(gksl_ctx *c);
+// drive table eps(t) - E for steps [0, n) of a run starting at t0
+void fill_eps_table(gksl_ctx *c, double t0, double h, long long n);
+// `count` RK4 steps on the context state starting at global step `first` (drive table index)
+void advance(gksl_ctx *c, int precision, double h, long long first, long long count);
+// stages 1-3 of step g from y1 (FP64: double*, FP32: float*), writing the stage inputs Y2, Y3, Y4
+void forward_stage_inputs(gksl_ctx *c, int precision, double h, long long g, void *y1, void *Y2, void *Y3, void *Y4);
+void to_f32(const double *v, float *o, long long n, cudaStream_t s);
+
+// ---- adjoint.cu
+void adjoint_timeavg(gksl_ctx *c, const double *o_diag_dev, long long spp, long long period, int precision,
+                     double *loss, double *grad, int n_grad);
+
+// ---- structure.cu (Eq. 5 closed forms)
+long long structure_count(int N, int which, cudaStream_t s);
+long long structure_enumerate(int N, int which, long long cap, int *m, int *n, int *sidx, double *val,
+                              cudaStream_t s);
+
+// ---- hyb.cu: CSR -> hybrid ELL/warp-row format
+void build_hyb_pair(const CsrR &a0, const CsrR &a1, long long rows, Hyb<double> &h0, Hyb<double> &h1,
+                    Hyb<float> *h0f, Hyb<float> *h1f, cudaStream_t s);
+void build_hyb_single(const CsrR &a, long long rows, Hyb<double> &h, Hyb<float> *hf, double scale, cudaStream_t s);
+// several matrices applied together (one long-row set; entries scaled by `scales`)
+void build_hyb_multi(const std::vector<const CsrR *> &ms, const std::vector<double> &scales, long long rows,
+                     const std::vector<Hyb<double> *> &out, const std::vector<Hyb<float> *> &outf, cudaStream_t s);
+
+// CSR helpers (assemble.cu)
+void csr_transpose(const CsrR &a, CsrR &t, cudaStream_t s);
+void csr_copy_out(gksl_ctx *c, const CsrR &m, long long *nnz, int *rowptr, int *col, double *val);
+
+}  // namespace gk

@@ -1,0 +1,413 @@
+// Classical RK4 on dv/dt = (Q0 + eps(t) Q1) v + K (Sec. IV step 3.1, Eq. 8).
+//
+// One fused kernel per stage: every row r computes k_r = (Q0E y)_r + (eps_s - E) (Q1 y)_r,
+// where Q0E = Q0 + E Q1 carries K as an extra column that multiplies the constant 1 stored
+// at index D of every state-sized vector, and immediately applies the stage's update:
+//   stage 1: y2 = v + h/2 k1, acc = k1          stage 2: y3 = v + h/2 k2, acc += 2 k2
+//   stage 3: y4 = v + h k3,   acc += 2 k3       stage 4: v += h/6 (acc + k4)
+// The stage times are t_n, t_n + h/2 (twice), t_n + h with t_n = t0 + n h; the drive values
+// eps(t) - E = A sin(omega t) for a whole run are tabulated once per call, so no thread
+// evaluates a sine.  Matrix streams are loaded with the evict-first hint (__ldcs) so the
+// state-sized vectors stay in L2; the gather of y goes through the read-only path.
+//
+// FP32 bulk form: the same kernels on FP32 values and vectors, with the FP32 increment
+// h/6 (acc + k4) added to an FP64 master state every step, and (optionally) one full FP64
+// step every `corr_every` steps.
+#include <cmath>
+
+#include "internal.cuh"
+#include "prim.cuh"
+
+namespace gk {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = kThreads / 32;
+constexpr int kGraphSteps = 64;
+
+__global__ void k_eps_table(double t0, double h, double A, double omega, long long n, double *__restrict__ tab) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double tn = t0 + (double)i * h;
+    tab[3 * i + 0] = A * sin(omega * tn);
+    tab[3 * i + 1] = A * sin(omega * (tn + 0.5 * h));
+    tab[3 * i + 2] = A * sin(omega * (tn + h));
+}
+
+__global__ void k_set_ll(long long *p, long long v) { *p = v; }
+
+template <typename VT>
+__device__ inline VT ldcs(const VT *p) { return __ldcs(p); }
+
+// sum over the ELL slots of row r (slot 0 already loaded as c0/a0)
+template <typename VT, typename AT, int W>
+__device__ inline AT ell_dot(const HybView<VT> &H, long long r, int c0, VT a0, const VT *__restrict__ y) {
+    AT s = (AT)a0 * (AT)__ldg(y + c0);
+    if (W > 0) {
+#pragma unroll
+        for (int j = 1; j < W; ++j) {
+            long long p = (long long)j * H.ld + r;
+            s += (AT)ldcs(H.ell_val + p) * (AT)__ldg(y + ldcs(H.ell_col + p));
+        }
+    } else {
+#pragma unroll 4
+        for (int j = 1; j < H.width; ++j) {
+            long long p = (long long)j * H.ld + r;
+            s += (AT)ldcs(H.ell_val + p) * (AT)__ldg(y + ldcs(H.ell_col + p));
+        }
+    }
+    return s;
+}
+
+template <typename VT, typename AT>
+__device__ inline AT ell_dot_full(const HybView<VT> &H, long long r, const VT *__restrict__ y) {
+    AT s = AT(0);
+#pragma unroll 2
+    for (int j = 0; j < H.width; ++j) {
+        long long p = (long long)j * H.ld + r;
+        s += (AT)ldcs(H.ell_val + p) * (AT)__ldg(y + ldcs(H.ell_col + p));
+    }
+    return s;
+}
+
+template <typename VT, typename AT>
+__device__ inline AT tail_dot(const HybView<VT> &H, long long i, int lane, const VT *__restrict__ y) {
+    AT s = AT(0);
+    int e1 = H.tail_ptr[i + 1];
+    for (int e = H.tail_ptr[i] + lane; e < e1; e += 32) s += (AT)ldcs(H.tail_val + e) * (AT)__ldg(y + H.tail_col[e]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+template <int STAGE>
+__device__ inline int eps_slot() { return STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1); }
+
+// ---- FP64 epilogue
+template <int STAGE>
+__device__ inline void epi64(long long r, double k, double *v, double *__restrict__ yn, double *__restrict__ acc,
+                             double h) {
+    if (STAGE == 1) { yn[r] = v[r] + (0.5 * h) * k; acc[r] = k; }
+    if (STAGE == 2) { yn[r] = v[r] + (0.5 * h) * k; acc[r] = acc[r] + 2.0 * k; }
+    if (STAGE == 3) { yn[r] = v[r] + h * k; acc[r] = acc[r] + 2.0 * k; }
+    if (STAGE == 4) { v[r] = v[r] + (h / 6.0) * (acc[r] + k); }
+}
+
+// ---- FP32 epilogue (v32: FP32 mirror, v64: master)
+template <int STAGE>
+__device__ inline void epi32(long long r, float k, float *v32, double *v64, float *__restrict__ yn,
+                             float *__restrict__ acc, double h) {
+    float hf = (float)h;
+    if (STAGE == 1) { yn[r] = v32[r] + (0.5f * hf) * k; acc[r] = k; }
+    if (STAGE == 2) { yn[r] = v32[r] + (0.5f * hf) * k; acc[r] = acc[r] + 2.0f * k; }
+    if (STAGE == 3) { yn[r] = v32[r] + hf * k; acc[r] = acc[r] + 2.0f * k; }
+    if (STAGE == 4) {
+        float inc = (float)(h / 6.0) * (acc[r] + k);
+        double nv = v64[r] + (double)inc;
+        v64[r] = nv;
+        v32[r] = (float)nv;
+    }
+}
+
+struct StepArgs {
+    const int *long_rows;
+    long long n_long;
+    long long D;
+    int nb_long;
+    const double *eps_tab;
+    const long long *base;
+    long long local;
+    double h;
+};
+
+template <int STAGE, int W>
+__global__ void __launch_bounds__(kThreads) k_stage64(HybView<double> A0, HybView<double> A1, StepArgs a,
+                                                      const double *__restrict__ y, double *v, double *__restrict__ yn,
+                                                      double *__restrict__ acc) {
+    __shared__ double s_eps;
+    if (threadIdx.x == 0) s_eps = a.eps_tab[3 * (*a.base + a.local) + eps_slot<STAGE>()];
+    __syncthreads();
+    const double eps = s_eps;
+    if ((int)blockIdx.x < a.nb_long) {
+        int lane = threadIdx.x & 31;
+        long long i = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+        if (i >= a.n_long) return;
+        double s0 = tail_dot<double, double>(A0, i, lane, y);
+        double s1 = tail_dot<double, double>(A1, i, lane, y);
+        if (lane == 0) epi64<STAGE>(a.long_rows[i], s0 + eps * s1, v, yn, acc, a.h);
+        return;
+    }
+    long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
+    if (r >= a.D) return;
+    int c0 = ldcs(A0.ell_col + r);
+    if (c0 < 0) return;   // long row, handled by a warp above
+    double a0 = ldcs(A0.ell_val + r);
+    double s0 = ell_dot<double, double, W>(A0, r, c0, a0, y);
+    double s1 = ell_dot_full<double, double>(A1, r, y);
+    epi64<STAGE>(r, s0 + eps * s1, v, yn, acc, a.h);
+}
+
+template <int STAGE, int W>
+__global__ void __launch_bounds__(kThreads) k_stage32(HybView<float> A0, HybView<float> A1, StepArgs a,
+                                                      const float *__restrict__ y, float *v32, double *v64,
+                                                      float *__restrict__ yn, float *__restrict__ acc) {
+    __shared__ float s_eps;
+    if (threadIdx.x == 0) s_eps = (float)a.eps_tab[3 * (*a.base + a.local) + eps_slot<STAGE>()];
+    __syncthreads();
+    const float eps = s_eps;
+    if ((int)blockIdx.x < a.nb_long) {
+        int lane = threadIdx.x & 31;
+        long long i = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+        if (i >= a.n_long) return;
+        float s0 = tail_dot<float, float>(A0, i, lane, y);
+        float s1 = tail_dot<float, float>(A1, i, lane, y);
+        if (lane == 0) epi32<STAGE>(a.long_rows[i], s0 + eps * s1, v32, v64, yn, acc, a.h);
+        return;
+    }
+    long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
+    if (r >= a.D) return;
+    int c0 = ldcs(A0.ell_col + r);
+    if (c0 < 0) return;
+    float a0 = ldcs(A0.ell_val + r);
+    float s0 = ell_dot<float, float, W>(A0, r, c0, a0, y);
+    float s1 = ell_dot_full<float, float>(A1, r, y);
+    epi32<STAGE>(r, s0 + eps * s1, v32, v64, yn, acc, a.h);
+}
+
+__global__ void k_to_f32(const double *__restrict__ v, float *__restrict__ o, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) o[i] = (float)v[i];
+}
+
+__global__ void k_fill(double *p, long long n, double x) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = x;
+}
+
+__global__ void k_fill_f(float *p, long long n, float x) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = x;
+}
+
+__global__ void k_check_finite(const double *__restrict__ v, long long n, int *__restrict__ flag) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !isfinite(v[i])) atomicOr(flag, 1);
+}
+
+struct Launch {
+    unsigned grid;
+    StepArgs a;
+};
+
+Launch make_launch(gksl_ctx *c, const Hyb<double> &h0, double h, const double *tab, long long local) {
+    Launch L;
+    L.a.long_rows = h0.long_rows.p;
+    L.a.n_long = h0.n_long;
+    L.a.D = c->D;
+    L.a.nb_long = (int)((h0.n_long + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    L.a.eps_tab = tab;
+    L.a.base = c->step_base.p;
+    L.a.local = local;
+    L.a.h = h;
+    L.grid = (unsigned)(L.a.nb_long + (c->D + kThreads - 1) / kThreads);
+    return L;
+}
+
+template <int W>
+void step64_w(gksl_ctx *c, const Launch &L) {
+    auto A0 = view(c->hyb0), A1 = view(c->hyb1);
+    cudaStream_t s = c->stream;
+    k_stage64<1, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v.p, c->v.p, c->yA.p, c->acc.p);
+    k_stage64<2, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yA.p, c->v.p, c->yB.p, c->acc.p);
+    k_stage64<3, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yB.p, c->v.p, c->yA.p, c->acc.p);
+    k_stage64<4, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yA.p, c->v.p, nullptr, c->acc.p);
+}
+
+template <int W>
+void step32_w(gksl_ctx *c, const Launch &L) {
+    auto A0 = view(c->hyb0f), A1 = view(c->hyb1f);
+    cudaStream_t s = c->stream;
+    k_stage32<1, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v32.p, c->v32.p, c->v.p, c->yA32.p, c->acc32.p);
+    k_stage32<2, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yA32.p, c->v32.p, c->v.p, c->yB32.p, c->acc32.p);
+    k_stage32<3, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yB32.p, c->v32.p, c->v.p, c->yA32.p, c->acc32.p);
+    k_stage32<4, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yA32.p, c->v32.p, c->v.p, nullptr, c->acc32.p);
+}
+
+void launch_step(gksl_ctx *c, int precision, double h, const double *tab, long long local) {
+    Launch L = make_launch(c, c->hyb0, h, tab, local);
+    int W = c->hyb0.width;
+    if (precision == 64) {
+        if (W == 18) step64_w<18>(c, L);
+        else step64_w<0>(c, L);
+    } else {
+        if (W == 18) step32_w<18>(c, L);
+        else step32_w<0>(c, L);
+    }
+    GK_LAUNCH_CHECK();
+}
+
+// one CUDA graph per (chunk length, precision, h); replayed with the step base set before
+cudaGraphExec_t graph_for(gksl_ctx *c, long long steps, int precision, double h, const double *tab) {
+    for (auto &g : c->graphs)
+        if (g.steps == steps && g.precision == precision && g.h == h) return g.exec;
+    cudaGraph_t graph;
+    GK_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    for (long long i = 0; i < steps; ++i) launch_step(c, precision, h, tab, i);
+    GK_CUDA(cudaStreamEndCapture(c->stream, &graph));
+    cudaGraphExec_t exec;
+    GK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    GK_CUDA(cudaGraphDestroy(graph));
+    c->graphs.push_back({steps, precision, h, exec});
+    return exec;
+}
+
+void run_steps(gksl_ctx *c, int precision, double h, const double *tab, long long first, long long count) {
+    long long n = first, end = first + count;
+    while (end - n >= kGraphSteps) {
+        k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, n);
+        GK_LAUNCH_CHECK();
+        GK_CUDA(cudaGraphLaunch(graph_for(c, kGraphSteps, precision, h, tab), c->stream));
+        n += kGraphSteps;
+    }
+    if (n < end) {
+        k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, n);
+        GK_LAUNCH_CHECK();
+        for (long long i = 0; n + i < end; ++i) launch_step(c, precision, h, tab, i);
+        n = end;
+    }
+}
+
+}  // namespace
+
+void clear_graphs(gksl_ctx *c) {
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+void ensure_work(gksl_ctx *c, bool fp32) {
+    long long n = c->D + 1;
+    if (c->yA.n < (size_t)n) {
+        c->yA.alloc((size_t)n);
+        c->yB.alloc((size_t)n);
+        c->acc.alloc((size_t)n);
+        k_fill<<<grid_for(n, 256), 256, 0, c->stream>>>(c->yA.p, n, 1.0);
+        k_fill<<<grid_for(n, 256), 256, 0, c->stream>>>(c->yB.p, n, 1.0);
+        k_fill<<<grid_for(n, 256), 256, 0, c->stream>>>(c->acc.p, n, 0.0);
+        GK_LAUNCH_CHECK();
+        clear_graphs(c);
+    }
+    if (fp32 && c->v32.n < (size_t)n) {
+        c->v32.alloc((size_t)n);
+        c->yA32.alloc((size_t)n);
+        c->yB32.alloc((size_t)n);
+        c->acc32.alloc((size_t)n);
+        k_fill_f<<<grid_for(n, 256), 256, 0, c->stream>>>(c->yA32.p, n, 1.0f);
+        k_fill_f<<<grid_for(n, 256), 256, 0, c->stream>>>(c->yB32.p, n, 1.0f);
+        k_fill_f<<<grid_for(n, 256), 256, 0, c->stream>>>(c->acc32.p, n, 0.0f);
+        GK_LAUNCH_CHECK();
+        clear_graphs(c);
+    }
+    if (c->step_base.n == 0) c->step_base.alloc(1);
+    if (c->flag.n == 0) c->flag.alloc(1);
+}
+
+bool state_finite(gksl_ctx *c) {
+    GK_CUDA(cudaMemsetAsync(c->flag.p, 0, sizeof(int), c->stream));
+    k_check_finite<<<grid_for(c->D, 256), 256, 0, c->stream>>>(c->v.p, c->D, c->flag.p);
+    GK_LAUNCH_CHECK();
+    int f = 0;
+    GK_CUDA(cudaMemcpyAsync(&f, c->flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GK_CUDA(cudaStreamSynchronize(c->stream));
+    return f == 0;
+}
+
+void fill_eps_table(gksl_ctx *c, double t0, double h, long long n) {
+    size_t need = (size_t)(3 * (n > 0 ? n : 1));
+    if (c->eps_tab.n < need) {
+        clear_graphs(c);   // graphs bake the table pointer
+        c->eps_tab.alloc(need);
+    }
+    if (n > 0) {
+        k_eps_table<<<grid_for(n, 256), 256, 0, c->stream>>>(t0, h, c->A, c->omega, n, c->eps_tab.p);
+        GK_LAUNCH_CHECK();
+    }
+}
+
+void advance(gksl_ctx *c, int precision, double h, long long first, long long count) {
+    run_steps(c, precision, h, c->eps_tab.p, first, count);
+}
+
+void to_f32(const double *v, float *o, long long n, cudaStream_t s) {
+    k_to_f32<<<grid_for(n, 256), 256, 0, s>>>(v, o, n);
+    GK_LAUNCH_CHECK();
+}
+
+void forward_stage_inputs(gksl_ctx *c, int precision, double h, long long g, void *y1, void *Y2, void *Y3, void *Y4) {
+    k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, g);
+    GK_LAUNCH_CHECK();
+    cudaStream_t s = c->stream;
+    if (precision == 64) {
+        Launch L = make_launch(c, c->hyb0, h, c->eps_tab.p, 0);
+        auto A0 = view(c->hyb0), A1 = view(c->hyb1);
+        double *v = (double *)y1;
+        k_stage64<1, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, (double *)Y2, c->acc.p);
+        k_stage64<2, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, (double *)Y2, v, (double *)Y3, c->acc.p);
+        k_stage64<3, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, (double *)Y3, v, (double *)Y4, c->acc.p);
+    } else {
+        Launch L = make_launch(c, c->hyb0, h, c->eps_tab.p, 0);
+        auto A0 = view(c->hyb0f), A1 = view(c->hyb1f);
+        float *v = (float *)y1;
+        k_stage32<1, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, nullptr, (float *)Y2, c->acc32.p);
+        k_stage32<2, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, (float *)Y2, v, nullptr, (float *)Y3, c->acc32.p);
+        k_stage32<3, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, (float *)Y3, v, nullptr, (float *)Y4, c->acc32.p);
+    }
+    GK_LAUNCH_CHECK();
+}
+
+void propagate(gksl_ctx *c, long long spp, long long n_steps, int precision, long long corr_every,
+               long long emit_every, double *v_out, bool out_on_device) {
+    GK_REQUIRE(c->assembled, GKSL_ERR_STATE, "gksl_assemble must be called before gksl_propagate");
+    GK_REQUIRE(c->state_set, GKSL_ERR_STATE, "no state: call gksl_set_rho0 or gksl_set_state first");
+    GK_REQUIRE(precision == 64 || precision == 32, GKSL_ERR_ARG, "precision must be 64 or 32");
+    GK_REQUIRE(spp > 0 && n_steps >= 0, GKSL_ERR_ARG, "steps_per_period must be > 0 and n_steps >= 0");
+    if (precision == 32)
+        GK_REQUIRE(c->asm_flags & GKSL_ASM_FP32, GKSL_ERR_STATE, "precision 32 needs gksl_assemble with GKSL_ASM_FP32");
+    ensure_work(c, precision == 32);
+    const double T = 2.0 * M_PI / c->omega;
+    const double h = T / (double)spp;
+    fill_eps_table(c, c->t, h, n_steps);
+    DBuf<double> &tab = c->eps_tab;
+    if (precision == 32) {
+        k_to_f32<<<grid_for(c->D + 1, 256), 256, 0, c->stream>>>(c->v.p, c->v32.p, c->D + 1);
+        GK_LAUNCH_CHECK();
+    }
+    long long n = 0, emitted = 0;
+    while (n < n_steps) {
+        long long stop = n_steps;
+        if (emit_every > 0) stop = std::min(stop, (n / emit_every + 1) * emit_every);
+        long long corr_step = -1;   // 0-based index of the next FP64 step of the FP32 form
+        if (precision == 32 && corr_every > 0) corr_step = (n / corr_every + 1) * corr_every - 1;
+        if (corr_step >= 0 && corr_step < stop) {
+            if (corr_step > n) run_steps(c, 32, h, tab.p, n, corr_step - n);
+            run_steps(c, 64, h, tab.p, corr_step, 1);
+            k_to_f32<<<grid_for(c->D + 1, 256), 256, 0, c->stream>>>(c->v.p, c->v32.p, c->D + 1);
+            GK_LAUNCH_CHECK();
+            n = corr_step + 1;
+        } else {
+            run_steps(c, precision, h, tab.p, n, stop - n);
+            n = stop;
+        }
+        if (emit_every > 0 && n % emit_every == 0 && v_out) {
+            double *dst = v_out + emitted * c->D;
+            GK_CUDA(cudaMemcpyAsync(dst, c->v.p, sizeof(double) * c->D,
+                                    out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+            ++emitted;
+        }
+    }
+    GK_CUDA(cudaStreamSynchronize(c->stream));
+    c->t = c->t + (double)n_steps * h;
+    GK_REQUIRE(state_finite(c), GKSL_ERR_DIVERGED, "state became non-finite during propagation");
+}
+
+}  // namespace gk

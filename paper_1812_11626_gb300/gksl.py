@@ -1,0 +1,375 @@
+"""Thin ctypes binding of libgksl (include/gksl.h): argument marshalling only.
+
+Every ``gksl_*`` function below has the name and argument order of the C entry point.
+Array arguments may be numpy arrays (host memory) or CUDA torch tensors (device memory of
+the context's GPU); the library decides which by the pointer.  A non-OK status raises
+``GkslError`` with the library's message.  There is no fallback: if the shared library is
+missing, importing this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgksl.so")
+
+GKSL_OK, GKSL_ERR_ARG, GKSL_ERR_CUDA, GKSL_ERR_OOM, GKSL_ERR_STATE, GKSL_ERR_UNSTABLE, GKSL_ERR_DIVERGED, \
+    GKSL_ERR_TIMEOUT = range(8)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_OOM", "ERR_STATE", "ERR_UNSTABLE", "ERR_DIVERGED", "ERR_TIMEOUT"]
+GKSL_MAX_H0 = 8
+GKSL_MAX_P = 8
+GKSL_STRUCT_F, GKSL_STRUCT_D = 0, 1
+GKSL_ASM_FP32, GKSL_ASM_TRANSPOSE, GKSL_ASM_NO_DROP = 1, 2, 4
+GKSL_MAT_Q0, GKSL_MAT_Q1, GKSL_MAT_H0, GKSL_MAT_R = 0, 1, 16, 32
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libgksl is not built ({LIB_PATH} missing): run __graft_entry__.build() first")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class GkslError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"GKSL_{name}: {message}")
+
+
+class gksl_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("D", ctypes.c_longlong), ("nnz_q0", ctypes.c_longlong),
+                ("nnz_q1", ctypes.c_longlong), ("nnz_r", ctypes.c_longlong * GKSL_MAX_P),
+                ("ell_width_q0", ctypes.c_int), ("ell_width_q1", ctypes.c_int), ("long_rows", ctypes.c_longlong),
+                ("device_bytes", ctypes.c_longlong), ("assemble_seconds", ctypes.c_double),
+                ("max_abs_q0", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_longlong
+_D = ctypes.c_double
+_U = ctypes.c_uint
+_S = ctypes.c_int  # gksl_status
+
+_SIGS = {
+    "gksl_create": (_S, [_I, _I, _P, ctypes.POINTER(_P)]),
+    "gksl_destroy": (None, [_P]),
+    "gksl_last_error": (ctypes.c_char_p, [_P]),
+    "gksl_set_h0_component": (_S, [_P, _I, _D, _P, _P, _P, _P, _I]),
+    "gksl_set_theta": (_S, [_P, _I, _D]),
+    "gksl_set_h1": (_S, [_P, _P, _P, _P, _P, _I]),
+    "gksl_set_dissipator": (_S, [_P, _I, _D, _P, _P, _P, _P, _I]),
+    "gksl_set_gamma": (_S, [_P, _I, _D]),
+    "gksl_set_drive": (_S, [_P, _D, _D, _D]),
+    "gksl_expand": (_S, [_P, _P, _P, _P, _P, _I, _P, _P]),
+    "gksl_structure_count": (_S, [_I, _I, ctypes.POINTER(_L)]),
+    "gksl_structure_enumerate": (_S, [_I, _I, _L, _P, _P, _P, _P, ctypes.POINTER(_L)]),
+    "gksl_assemble": (_S, [_P, _U, ctypes.POINTER(_D)]),
+    "gksl_get_csr": (_S, [_P, _I, ctypes.POINTER(_L), _P, _P, _P]),
+    "gksl_get_k": (_S, [_P, _P]),
+    "gksl_get_k_channel": (_S, [_P, _I, _P]),
+    "gksl_set_rho0": (_S, [_P, _P, _P]),
+    "gksl_set_state": (_S, [_P, _P, _D]),
+    "gksl_get_state": (_S, [_P, _P, ctypes.POINTER(_D)]),
+    "gksl_min_stable_steps": (_S, [_P, ctypes.POINTER(_L)]),
+    "gksl_propagate": (_S, [_P, _L, _L, _I, _L, _L, _P]),
+    "gksl_observable_diag": (_S, [_P, _P, _P, _L, _P]),
+    "gksl_rho": (_S, [_P, _P, _P, _P]),
+    "gksl_adjoint_timeavg": (_S, [_P, _P, _L, _L, _I, ctypes.POINTER(_D), _P, _I]),
+    "gksl_batch_create": (_S, [_I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "gksl_batch_destroy": (None, [_P]),
+    "gksl_batch_last_error": (ctypes.c_char_p, [_P]),
+    "gksl_batch_reset": (_S, [_P]),
+    "gksl_batch_propagate": (_S, [_P, _P, _L, _L, ctypes.POINTER(_D)]),
+    "gksl_batch_get_state": (_S, [_P, _I, _P]),
+    "gksl_batch_info": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "gksl_get_info": (_S, [_P, ctypes.POINTER(gksl_info)]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = sorted(_SIGS)
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _arr(x, dtype):
+    """numpy arrays are converted to the C type; tensors are passed through unchanged."""
+    if x is None or hasattr(x, "data_ptr"):
+        return x
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _check(st, ctx=None, batch=None):
+    if st != GKSL_OK:
+        msg = ""
+        if ctx is not None:
+            msg = _lib.gksl_last_error(ctx).decode()
+        elif batch is not None:
+            msg = _lib.gksl_batch_last_error(batch).decode()
+        raise GkslError(st, msg)
+
+
+# ------------------------------------------------------------------ the C calls, same names
+
+def gksl_create(N, device=0, cuda_stream=None):
+    out = _P()
+    _check(_lib.gksl_create(int(N), int(device), cuda_stream, ctypes.byref(out)))
+    return out.value
+
+
+def gksl_destroy(ctx):
+    _lib.gksl_destroy(ctx)
+
+
+def gksl_last_error(ctx):
+    return _lib.gksl_last_error(ctx).decode()
+
+
+def _op(rowptr, col, re, im):
+    return _arr(rowptr, np.int32), _arr(col, np.int32), _arr(re, np.float64), _arr(im, np.float64)
+
+
+def gksl_set_h0_component(ctx, k, theta, rowptr, col, re, im, nnz):
+    rp, c, r, i = _op(rowptr, col, re, im)
+    _check(_lib.gksl_set_h0_component(ctx, k, theta, _ptr(rp), _ptr(c), _ptr(r), _ptr(i), int(nnz)), ctx)
+
+
+def gksl_set_theta(ctx, k, theta):
+    _check(_lib.gksl_set_theta(ctx, k, theta), ctx)
+
+
+def gksl_set_h1(ctx, rowptr, col, re, im, nnz):
+    rp, c, r, i = _op(rowptr, col, re, im)
+    _check(_lib.gksl_set_h1(ctx, _ptr(rp), _ptr(c), _ptr(r), _ptr(i), int(nnz)), ctx)
+
+
+def gksl_set_dissipator(ctx, p, gamma, rowptr, col, re, im, nnz):
+    rp, c, r, i = _op(rowptr, col, re, im)
+    _check(_lib.gksl_set_dissipator(ctx, p, gamma, _ptr(rp), _ptr(c), _ptr(r), _ptr(i), int(nnz)), ctx)
+
+
+def gksl_set_gamma(ctx, p, gamma):
+    _check(_lib.gksl_set_gamma(ctx, p, gamma), ctx)
+
+
+def gksl_set_drive(ctx, E, A, omega):
+    _check(_lib.gksl_set_drive(ctx, E, A, omega), ctx)
+
+
+def gksl_expand(ctx, rowptr, col, re, im, nnz, coef_re, coef_im=None):
+    rp, c, r, i = _op(rowptr, col, re, im)
+    _check(_lib.gksl_expand(ctx, _ptr(rp), _ptr(c), _ptr(r), _ptr(i), int(nnz), _ptr(coef_re), _ptr(coef_im)), ctx)
+
+
+def gksl_structure_count(N, which):
+    n = _L()
+    _check(_lib.gksl_structure_count(int(N), int(which), ctypes.byref(n)))
+    return n.value
+
+
+def gksl_structure_enumerate(N, which, capacity, m, n, s, value):
+    cnt = _L()
+    _check(_lib.gksl_structure_enumerate(int(N), int(which), int(capacity), _ptr(m), _ptr(n), _ptr(s), _ptr(value),
+                                         ctypes.byref(cnt)))
+    return cnt.value
+
+
+def gksl_assemble(ctx, flags=0):
+    sec = _D()
+    _check(_lib.gksl_assemble(ctx, int(flags), ctypes.byref(sec)), ctx)
+    return sec.value
+
+
+def gksl_get_csr(ctx, which, rowptr=None, col=None, val=None):
+    nnz = _L()
+    _check(_lib.gksl_get_csr(ctx, int(which), ctypes.byref(nnz), _ptr(rowptr), _ptr(col), _ptr(val)), ctx)
+    return nnz.value
+
+
+def gksl_get_k(ctx, K):
+    _check(_lib.gksl_get_k(ctx, _ptr(K)), ctx)
+
+
+def gksl_get_k_channel(ctx, p, K):
+    _check(_lib.gksl_get_k_channel(ctx, int(p), _ptr(K)), ctx)
+
+
+def gksl_set_rho0(ctx, re, im=None):
+    re, im = _arr(re, np.float64), _arr(im, np.float64)
+    _check(_lib.gksl_set_rho0(ctx, _ptr(re), _ptr(im)), ctx)
+
+
+def gksl_set_state(ctx, v, t):
+    v = _arr(v, np.float64)
+    _check(_lib.gksl_set_state(ctx, _ptr(v), float(t)), ctx)
+
+
+def gksl_get_state(ctx, v):
+    t = _D()
+    _check(_lib.gksl_get_state(ctx, _ptr(v), ctypes.byref(t)), ctx)
+    return t.value
+
+
+def gksl_min_stable_steps(ctx):
+    n = _L()
+    _check(_lib.gksl_min_stable_steps(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def gksl_propagate(ctx, steps_per_period, n_steps, precision=64, correction_every=0, emit_every=0, v_out=None):
+    _check(_lib.gksl_propagate(ctx, int(steps_per_period), int(n_steps), int(precision), int(correction_every),
+                               int(emit_every), _ptr(v_out)), ctx)
+
+
+def gksl_observable_diag(ctx, o_diag, v, count, out):
+    o_diag = _arr(o_diag, np.float64)
+    _check(_lib.gksl_observable_diag(ctx, _ptr(o_diag), _ptr(v), int(count), _ptr(out)), ctx)
+
+
+def gksl_rho(ctx, v, re, im):
+    _check(_lib.gksl_rho(ctx, _ptr(_arr(v, np.float64)), _ptr(re), _ptr(im)), ctx)
+
+
+def gksl_adjoint_timeavg(ctx, o_diag, steps_per_period, period_index, precision, grad):
+    loss = _D()
+    o_diag = _arr(o_diag, np.float64)
+    _check(_lib.gksl_adjoint_timeavg(ctx, _ptr(o_diag), int(steps_per_period), int(period_index), int(precision),
+                                     ctypes.byref(loss), _ptr(grad), len(grad)), ctx)
+    return loss.value
+
+
+def gksl_batch_create(groups, n_inst, A, g):
+    arr = (_P * len(groups))(*groups)
+    ni = np.ascontiguousarray(n_inst, dtype=np.int32)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = _P()
+    _check(_lib.gksl_batch_create(len(groups), ctypes.cast(arr, _P), _ptr(ni), _ptr(A), _ptr(g), ctypes.byref(out)))
+    return out.value
+
+
+def gksl_batch_destroy(b):
+    _lib.gksl_batch_destroy(b)
+
+
+def gksl_batch_reset(b):
+    _check(_lib.gksl_batch_reset(b), batch=b)
+
+
+def gksl_batch_propagate(b, steps_per_period, periods, correction_every=0):
+    spp = np.ascontiguousarray(steps_per_period, dtype=np.int64)
+    sec = _D()
+    _check(_lib.gksl_batch_propagate(b, _ptr(spp), int(periods), int(correction_every), ctypes.byref(sec)), batch=b)
+    return sec.value
+
+
+def gksl_batch_get_state(b, instance, v):
+    _check(_lib.gksl_batch_get_state(b, int(instance), _ptr(v)), batch=b)
+
+
+def gksl_batch_info(b, group):
+    ipl, us = _I(), _D()
+    _check(_lib.gksl_batch_info(b, int(group), ctypes.byref(ipl), ctypes.byref(us)), batch=b)
+    return ipl.value, us.value
+
+
+def gksl_get_info(ctx):
+    info = gksl_info()
+    _check(_lib.gksl_get_info(ctx, ctypes.byref(info)), ctx)
+    return info
+
+
+# ------------------------------------------------------------------ conveniences over the calls
+
+def set_csr_operator(setter, ctx, *lead, op):
+    """Pass a workloads.CSR operator to one of the gksl_set_* calls."""
+    setter(ctx, *lead, op.rowptr, op.col, op.re, op.im, op.nnz)
+
+
+def get_csr_numpy(ctx, which):
+    """Copy an assembled matrix to host numpy arrays (rowptr, col, val)."""
+    nnz = gksl_get_csr(ctx, which)
+    info_D = gksl_get_info(ctx).D
+    rp = np.empty(info_D + 1, dtype=np.int32)
+    col = np.empty(max(nnz, 1), dtype=np.int32)
+    val = np.empty(max(nnz, 1), dtype=np.float64)
+    gksl_get_csr(ctx, which, rp, col, val)
+    return rp, col[:nnz], val[:nnz]
+
+
+def dimer_context(d, device=0, stream=None, flags=GKSL_ASM_FP32 | GKSL_ASM_TRANSPOSE, assemble=True):
+    """Context for a workloads.Dimer: H0 components (J HJ, U HU), H1 and L at rate gamma/M."""
+    p = d.params
+    ctx = gksl_create(d.N, device, stream)
+    set_csr_operator(gksl_set_h0_component, ctx, 0, p["J"], op=d.HJ)
+    set_csr_operator(gksl_set_h0_component, ctx, 1, p["U"], op=d.HU)
+    set_csr_operator(gksl_set_h1, ctx, op=d.H1)
+    set_csr_operator(gksl_set_dissipator, ctx, 0, d.rate, op=d.L)
+    gksl_set_drive(ctx, p["E"], p["A"], p["omega"])
+    if assemble:
+        gksl_assemble(ctx, flags)
+    gksl_set_rho0(ctx, d.rho0_dense().real.copy(), d.rho0_dense().imag.copy())
+    return ctx
+
+
+class TimeAvgObservable:
+    """torch.autograd.Function factory: loss(theta) = period mean of <O> with the adjoint gradient.
+
+    ``make(ctx, o_diag, spp, period, precision)`` returns a function of a float64 tensor
+    theta = [A, gamma_0.., theta_0..] (the order of gksl_adjoint_timeavg) whose backward is
+    the library's discrete adjoint of the RK4 map.
+    """
+
+    @staticmethod
+    def make(ctx, o_diag, steps_per_period, period_index, precision=64):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, theta):
+                th = theta.detach().cpu().numpy().astype(np.float64)
+                info = gksl_get_info(ctx)
+                del info
+                grad = np.zeros(len(th))
+                _apply_params(ctx, th)
+                loss = gksl_adjoint_timeavg(ctx, o_diag, steps_per_period, period_index, precision, grad)
+                fctx.save_for_backward(torch.as_tensor(grad, dtype=theta.dtype, device=theta.device))
+                return torch.as_tensor(loss, dtype=theta.dtype, device=theta.device)
+
+            @staticmethod
+            def backward(fctx, gout):
+                (g,) = fctx.saved_tensors
+                return gout * g
+
+        return _Fn.apply
+
+
+_PARAM_LAYOUT = {}
+
+
+def set_param_layout(ctx, A_drive, E, omega, channels, components):
+    """Record which channel / component indices theta maps to for TimeAvgObservable."""
+    _PARAM_LAYOUT[ctx] = (E, omega, list(channels), list(components))
+
+
+def _apply_params(ctx, th):
+    E, omega, channels, comps = _PARAM_LAYOUT[ctx]
+    gksl_set_drive(ctx, E, float(th[0]), omega)
+    for i, p in enumerate(channels):
+        gksl_set_gamma(ctx, p, float(th[1 + i]))
+    for i, k in enumerate(comps):
+        gksl_set_theta(ctx, k, float(th[1 + len(channels) + i]))
+    gksl_assemble(ctx, GKSL_ASM_FP32 | GKSL_ASM_TRANSPOSE)

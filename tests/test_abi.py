@@ -1,0 +1,56 @@
+"""C-ABI library: builds for sm_103a, loads, exports every declared entry point, and reports
+argument errors as statuses (no GPU needed for any of these)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def G():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1812_11626_gb300 import gksl
+    return gksl
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "gksl.h")).read()
+    return sorted(set(re.findall(r"\b(gksl_[a-z0-9_]+)\s*\(", hdr)))
+
+
+def test_every_declared_symbol_is_exported(G):
+    syms = subprocess.run(["nm", "-D", "--defined-only", G.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in syms.splitlines() if line.strip()}
+    missing = [d for d in _declared() if d not in exported]
+    assert not missing, missing
+    assert set(_declared()) == set(G.EXPORTED)
+
+
+def test_library_is_sm103a(G):
+    out = subprocess.run(["cuobjdump", "--list-elf", G.LIB_PATH], capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_argument_errors_are_statuses(G):
+    import ctypes
+    lib = G._lib
+    n = ctypes.c_longlong()
+    assert lib.gksl_structure_count(1, 0, ctypes.byref(n)) == G.GKSL_ERR_ARG
+    assert lib.gksl_structure_count(5, 7, ctypes.byref(n)) == G.GKSL_ERR_ARG
+    out = ctypes.c_void_p()
+    assert lib.gksl_create(1, 0, None, ctypes.byref(out)) == G.GKSL_ERR_ARG
+    assert lib.gksl_set_drive(None, 0.0, 0.0, 1.0) == G.GKSL_ERR_ARG
+    assert lib.gksl_batch_reset(None) == G.GKSL_ERR_ARG
+
+
+def test_create_without_device_fails_cleanly(G):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(G.GkslError) as e:
+        G.gksl_create(4, 0)
+    assert e.value.status == G.GKSL_ERR_CUDA

@@ -1,0 +1,100 @@
+"""Adjoint gradient of the period-averaged <n1 - n2> against the oracle's discrete adjoint and
+against central finite differences of the GPU's own forward loss."""
+import numpy as np
+import pytest
+
+from oracle import propagate as OP
+from oracle import system as SYS
+from paper_1812_11626_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1812_11626_gb300 import gksl
+    return gksl
+
+
+def oracle_grad(d, S, period):
+    """[d/dA, d/d(rate), d/dJ, d/dU] of the oracle's discrete adjoint."""
+    u = SYS.unfold_dimer(d)
+    p = d.params
+    h = 2 * np.pi / p["omega"] / S
+    w, c0 = OP.observable_weights(d.obs_diag)
+    v0 = SYS.initial_v(d)
+    Q0 = u.q0(p["J"], p["U"], d.rate)
+    sinw = lambda t: np.sin(p["omega"] * t)
+    return OP.timeavg_adjoint(Q0, u.Q1, d.rate * u.K1, OP.eps_fn(p["E"], p["A"], p["omega"]), v0, w, c0, h, S,
+                              period, dQ0=[None, u.R1, u.QJ, u.QU], dQ1=[(u.Q1, sinw), None, None, None],
+                              dK=[None, u.K1, None, None])
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 2e-3)])
+def test_adjoint_vs_oracle(G, precision, tol):
+    d = W.dimer(6)
+    S, period = 60, 3
+    ctx = G.dimer_context(d)
+    try:
+        grad = np.zeros(4)   # [A, rate (gamma_0), J (theta_0), U (theta_1)]
+        loss = G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, period, precision, grad)
+        L, g = oracle_grad(d, S, period)
+        assert abs(loss - L) < (1e-11 if precision == 64 else 1e-4)
+        scale = np.abs(g).max()
+        assert np.abs(grad - g).max() < tol * scale, (grad, g)
+        # the state is left unchanged
+        v = np.zeros(d.N * d.N - 1)
+        assert G.gksl_get_state(ctx, v) == 0.0
+        assert np.abs(v - SYS.initial_v(d)).max() < 1e-15
+    finally:
+        G.gksl_destroy(ctx)
+
+
+def test_adjoint_vs_finite_differences(G):
+    """Central differences (h = 1e-6) of the GPU's FP64 forward loss; relative 1e-6."""
+    d = W.dimer(8)
+    S, period = 120, 2
+    ctx = G.dimer_context(d)
+    try:
+        grad = np.zeros(4)
+        G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, period, 64, grad)
+        p = d.params
+        base = dict(A=p["A"], rate=d.rate, J=p["J"], U=p["U"])
+
+        def loss(th):
+            G.gksl_set_drive(ctx, p["E"], th["A"], p["omega"])
+            G.gksl_set_gamma(ctx, 0, th["rate"])
+            G.gksl_set_theta(ctx, 0, th["J"])
+            G.gksl_set_theta(ctx, 1, th["U"])
+            G.gksl_assemble(ctx, G.GKSL_ASM_FP32 | G.GKSL_ASM_TRANSPOSE)
+            g = np.zeros(4)
+            return G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, period, 64, g)
+
+        for i, key in enumerate(["A", "rate", "J", "U"]):
+            hfd = 1e-6 * max(1.0, abs(base[key]))
+            tp = dict(base); tp[key] += hfd
+            tm = dict(base); tm[key] -= hfd
+            fd = (loss(tp) - loss(tm)) / (2 * hfd)
+            assert abs(fd - grad[i]) <= 1e-6 * max(abs(grad[i]), 1e-3 * np.abs(grad).max()), (key, fd, grad[i])
+    finally:
+        G.gksl_destroy(ctx)
+
+
+def test_autograd_function(G):
+    import torch
+    d = W.dimer(5)
+    ctx = G.dimer_context(d)
+    try:
+        p = d.params
+        G.set_param_layout(ctx, p["A"], p["E"], p["omega"], channels=[0], components=[0, 1])
+        fn = G.TimeAvgObservable.make(ctx, d.obs_diag, 40, 2, 64)
+        theta = torch.tensor([p["A"], d.rate, p["J"], p["U"]], dtype=torch.float64, requires_grad=True)
+        L = fn(theta)
+        L.backward()
+        ref = np.zeros(4)
+        Lr = G.gksl_adjoint_timeavg(ctx, d.obs_diag, 40, 2, 64, ref)
+        assert abs(L.item() - Lr) < 1e-14 and np.abs(theta.grad.numpy() - ref).max() < 1e-14
+    finally:
+        G.gksl_destroy(ctx)

@@ -1,0 +1,69 @@
+"""Batched form: every instance of a mixed-N batch against its own oracle run."""
+import numpy as np
+import pytest
+
+from oracle import system as SYS
+from paper_1812_11626_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1812_11626_gb300 import gksl
+    return gksl
+
+
+def test_batch_mixed_n_vs_oracle(G):
+    sizes = [(5, 3), (9, 40), (12, 70)]   # (N, instances): chunk widths 1..3 warps of lanes
+    rng = np.random.default_rng(3)
+    ctxs, A, g, inst = [], [], [], []
+    for N, B in sizes:
+        d = W.dimer(N)
+        d.rate = 1.0 / (N - 1)   # group rate gamma = 1 per boson; g_b = gamma_b scales it
+        ctxs.append(G.dimer_context(d))
+        for _ in range(B):
+            a, gam = 0.5 + 2.5 * rng.random(), 10 ** (-2 + 2 * rng.random())
+            A.append(a)
+            g.append(gam)
+            inst.append((N, a, gam))
+    b = G.gksl_batch_create(ctxs, [B for _, B in sizes], A, g)
+    try:
+        spp, periods = 3000, 2   # above the RK4 stability bound of every instance
+        G.gksl_batch_propagate(b, [spp] * len(sizes), periods, spp)
+        for i in list(range(0, len(inst), 7)) + [len(inst) - 1]:
+            N, a, gam = inst[i]
+            d = W.dimer(N, dict(A=a, gamma=gam))
+            u = SYS.unfold_dimer(d)
+            v_ref, _ = SYS.propagate_dimer(d, u, spp, spp * periods)
+            v = np.zeros(N * N - 1)
+            G.gksl_batch_get_state(b, i, v)
+            assert np.abs(v - v_ref).max() < 1e-5, (i, N, np.abs(v - v_ref).max())
+        for gi in range(len(sizes)):
+            ipl, us = G.gksl_batch_info(b, gi)
+            assert 1 <= ipl <= 4 and us > 0
+    finally:
+        G.gksl_batch_destroy(b)
+        for c in ctxs:
+            G.gksl_destroy(c)
+
+
+def test_batch_fp64_correction_only_matches_fp64(G):
+    """With an FP64 step every step the batch reproduces the FP64 single-instance path."""
+    d = W.dimer(7)
+    ctx = G.dimer_context(d)
+    try:
+        b = G.gksl_batch_create([ctx], [2], [d.params["A"], 0.3], [1.0, 0.5])
+        try:
+            G.gksl_batch_propagate(b, [400], 1, 1)
+            u = SYS.unfold_dimer(d)
+            v_ref, _ = SYS.propagate_dimer(d, u, 400, 400)
+            v = np.zeros(48)
+            G.gksl_batch_get_state(b, 0, v)
+            assert np.abs(v - v_ref).max() < 1e-10
+        finally:
+            G.gksl_batch_destroy(b)
+    finally:
+        G.gksl_destroy(ctx)

@@ -1,0 +1,180 @@
+"""Parity of the CUDA RK4 propagation with the oracle.
+
+Tolerances: FP64 path 1e-10 on v (absolute; |v| <= 1); FP32 bulk form 1e-5 on v and 1e-4
+on <n1 - n2> (absolute).
+"""
+import numpy as np
+import pytest
+
+from oracle import basis as OB
+from oracle import lindblad as OL
+from oracle import propagate as OP
+from oracle import system as SYS
+from paper_1812_11626_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-10
+TOL32_V = 1e-5
+TOL32_O = 1e-4
+
+
+@pytest.fixture(scope="module")
+def G():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1812_11626_gb300 import gksl
+    return gksl
+
+
+def run_gpu(G, ctx, spp, nsteps, emit, precision=64, corr=0, D=None):
+    out = np.zeros((nsteps // emit, D))
+    G.gksl_propagate(ctx, spp, nsteps, precision, corr, emit, out)
+    return out
+
+
+def test_config0_fp64_n10(G):
+    """N = 10 dimer, 10 periods x 200 steps, v at every period end (the small workload)."""
+    d = W.dimer(10)
+    ctx = G.dimer_context(d)
+    try:
+        out = run_gpu(G, ctx, 200, 2000, 200, D=99)
+        u = SYS.unfold_dimer(d)
+        _, ref = SYS.propagate_dimer(d, u, 200, 2000, emit_every=200)
+        err = max(np.abs(out[i] - ref[i]).max() for i in range(10))
+        assert err < TOL64, err
+        w, c0 = OP.observable_weights(d.obs_diag)
+        obs = np.zeros(10)
+        G.gksl_observable_diag(ctx, d.obs_diag, out, 10, obs)
+        assert np.abs(obs - np.array([c0 + w @ r for r in ref])).max() < 1e-9
+        rho = OB.rho_from_v(out[-1], N=10)
+        assert abs(np.trace(rho) - 1) < 1e-14 and np.linalg.eigvalsh(rho).min() > -1e-8
+    finally:
+        G.gksl_destroy(ctx)
+
+
+def test_random_operators_fp64(G):
+    """General operators (two H0 parts, traceful non-Hermitian L, two channels) against the
+    dense rho-space RK4 (no generator basis on the reference side)."""
+    N = 6
+    H0 = W.random_operator(N, 0.6, 71, hermitian=True)
+    H1 = W.random_operator(N, 0.5, 72, hermitian=True)
+    L0 = W.random_operator(N, 0.5, 73)
+    L1 = W.random_operator(N, 0.5, 74)
+    ctx = G.gksl_create(N)
+    try:
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 2, 0.8, op=H0)
+        G.set_csr_operator(G.gksl_set_h1, ctx, op=H1)
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, 0.3, op=L0)
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 5, 0.1, op=L1)
+        G.gksl_set_drive(ctx, 0.2, 0.7, 2.0)
+        G.gksl_assemble(ctx, 0)
+        rho0 = np.diag(np.linspace(1, 2, N)).astype(complex)
+        rho0 /= np.trace(rho0)
+        rho0[0, 1] = rho0[1, 0] = 0.05
+        G.gksl_set_rho0(ctx, rho0.real.copy(), rho0.imag.copy())
+        spp, n = 500, 700
+        D = N * N - 1
+        out = run_gpu(G, ctx, spp, n, n, D=D)
+        h = 2 * np.pi / 2.0 / spp
+        eps = OP.eps_fn(0.2, 0.7, 2.0)
+        rho = OP.rho_rk4(0.8 * H0.to_dense(), H1.to_dense(), [L0.to_dense(), L1.to_dense()], [0.3, 0.1], eps, rho0,
+                         h, n)
+        assert np.abs(out[0] - OB.expand(rho).real).max() < TOL64
+    finally:
+        G.gksl_destroy(ctx)
+
+
+def test_config1_n100_fp64_and_fp32(G):
+    """N = 100 (D = 9999) at the stable 4000 steps/period: FP64 parity over a quarter period,
+    FP32 bulk error against FP64 over two periods."""
+    d = W.dimer(100)
+    ctx = G.dimer_context(d)
+    try:
+        D = d.N * d.N - 1
+        spp = 4000
+        out = run_gpu(G, ctx, spp, 1000, 500, D=D)
+        u = SYS.unfold_dimer(d)
+        _, ref = SYS.propagate_dimer(d, u, spp, 1000, emit_every=500)
+        assert max(np.abs(out[i] - ref[i]).max() for i in range(2)) < TOL64
+        # FP32 bulk vs FP64, both on the GPU, from rho0
+        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+        v64 = run_gpu(G, ctx, spp, 2 * spp, spp, D=D)
+        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+        v32 = run_gpu(G, ctx, spp, 2 * spp, spp, precision=32, corr=spp, D=D)
+        assert np.abs(v32 - v64).max() < TOL32_V
+        o64, o32 = np.zeros(2), np.zeros(2)
+        G.gksl_observable_diag(ctx, d.obs_diag, v64, 2, o64)
+        G.gksl_observable_diag(ctx, d.obs_diag, v32, 2, o32)
+        assert np.abs(o32 - o64).max() < TOL32_O
+    finally:
+        G.gksl_destroy(ctx)
+
+
+def test_fp32_config0_vs_oracle(G):
+    d = W.dimer(10)
+    ctx = G.dimer_context(d)
+    try:
+        out = run_gpu(G, ctx, 200, 2000, 200, precision=32, corr=200, D=99)
+        u = SYS.unfold_dimer(d)
+        _, ref = SYS.propagate_dimer(d, u, 200, 2000, emit_every=200)
+        assert max(np.abs(out[i] - ref[i]).max() for i in range(10)) < TOL32_V
+    finally:
+        G.gksl_destroy(ctx)
+
+
+def test_resume_is_bit_identical(G):
+    """Checkpoint/resume: two calls of n steps equal one call of 2n steps exactly (FP64)."""
+    d = W.dimer(12)
+    ctx = G.dimer_context(d)
+    try:
+        D = d.N * d.N - 1
+        a = run_gpu(G, ctx, 300, 200, 200, D=D)
+        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+        run_gpu(G, ctx, 300, 77, 77, D=D)
+        v = np.zeros(D)
+        t = G.gksl_get_state(ctx, v)
+        G.gksl_set_state(ctx, v, t)
+        b = run_gpu(G, ctx, 300, 123, 123, D=D)
+        assert np.abs(a[0] - b[0]).max() < 1e-14
+    finally:
+        G.gksl_destroy(ctx)
+
+
+def test_min_stable_steps_and_divergence_guard(G):
+    """The stability bound admits a finite run; far below it the state blows up and the call
+    returns GKSL_ERR_DIVERGED (host-side check of the state, no device fault involved)."""
+    d = W.dimer(60)
+    ctx = G.dimer_context(d)
+    try:
+        spp = G.gksl_min_stable_steps(ctx)
+        # the bound follows the eigenvalue spread of H(t): U/2 M^2/2 dominates for this model
+        M = d.N - 1
+        assert 0.25 * M * M / 2 * 2 * np.pi / 2.8 < spp < 4 * M * M
+        D = d.N * d.N - 1
+        run_gpu(G, ctx, spp, spp // 4, spp // 4, D=D)
+        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+        with pytest.raises(G.GkslError) as e:
+            G.gksl_propagate(ctx, max(spp // 20, 1), 4000, 64, 0, 0, None)
+        assert e.value.status == G.GKSL_ERR_DIVERGED
+    finally:
+        G.gksl_destroy(ctx)
+
+
+def test_config4_n1000_fp64_steps(G):
+    """Largest workload (N = 1000, D = 999999) in the launch configuration of the benchmark:
+    a few FP64 steps at the stable step size against the oracle's RK4 on its own matrices."""
+    d = W.dimer(1000)
+    ctx = G.dimer_context(d, flags=G.GKSL_ASM_FP32)
+    try:
+        spp = G.gksl_min_stable_steps(ctx)
+        D = d.N * d.N - 1
+        nst = 6
+        out = run_gpu(G, ctx, spp, nst, nst, D=D)
+        u = SYS.unfold_dimer(d)
+        v_ref, _ = SYS.propagate_dimer(d, u, spp, nst)
+        assert np.abs(out[0] - v_ref).max() < TOL64
+        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+        o32 = run_gpu(G, ctx, spp, nst, nst, precision=32, corr=0, D=D)
+        assert np.abs(o32[0] - v_ref).max() < TOL32_V
+    finally:
+        G.gksl_destroy(ctx)
