@@ -1,0 +1,395 @@
+"""Benchmark: RK4 propagation of the unfolded driven Bose dimer at N = 1000 on GB300.
+
+One bench step = STEP_RK4 classical RK4 steps (FP64) of the N = 1000 dimer (D = 999 999
+Bloch components, Q0 with 18.4 M stored entries) at the stable step size, inputs resident in
+HBM.  Reported: RK4 steps/s (whole job), the roofline of the stage kernel, an end-to-end
+number through the C-ABI with host buffers, the CPU oracle timed on the host, and side
+measurements (FP32 bulk form, GPU assembly seconds, batched instances, adjoint gradient).
+
+--impl reference times the CPU oracle instead (the deliberately slow reference arm).
+Multi-GPU (torchrun): independent replicas, one per GPU, no collective on the data path.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BENCH = 1000
+STEP_RK4 = 2000          # RK4 steps per bench step
+METRIC = "RK4 steps/s & SpMV HBM GB/s at N=1000; Q/K assembly s; batched/adjoint vs plain"
+UNIT = "RK4 steps/s"
+PROFILE_JSON = os.path.join(ROOT, "profiles", "rk4_stage64_n1000.json")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, max clock, throttle reasons)."""
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                mx.append(float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for f in ("rk4.cu", "hyb.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1812_11626_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stage_bytes(nnz0, nnz1, D, precision):
+    """Compulsory bytes per RK4 stage launch, averaged over the 4 stages of a step.
+
+    Matrix stream: value + int32 column per stored entry of [Q0 + E Q1 | K] and Q1 (no row
+    pointers in the ELL layout).  Vectors, per step: stage 1 reads v once (also the gather
+    source) and writes y2 and acc; stages 2-3 gather y, read v, write y_next, read+write acc;
+    stage 4 gathers y4, reads+writes v, reads acc: 17 vector passes of D elements, plus the
+    FP64 master update (read+write) of the FP32 form.
+    """
+    vb = 8 if precision == 64 else 4
+    mat = (vb + 4) * (nnz0 + nnz1)
+    vec = 17 * vb * D + (16 * D if precision == 32 else 0)
+    return (4 * mat + vec) / 4.0
+
+
+def launches_per_call(n):
+    """Kernels one gksl_propagate(n steps, FP64) launches: 4 per step, a step-base setter per
+    64-step graph chunk and per remainder, the drive table and the final finiteness check."""
+    return 4 * n + (n // 64) + (1 if n % 64 else 0) + 2
+
+
+# ---------------------------------------------------------------------- reference arm (CPU oracle)
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import scipy.sparse  # noqa: F401
+    from oracle import native, propagate as OP, system as SYS
+    from paper_1812_11626_gb300 import workloads as W
+    native.build()
+    d = W.dimer(N_BENCH)
+    t0 = time.perf_counter()
+    u = SYS.unfold_dimer(d)
+    asm_s = time.perf_counter() - t0
+    p = d.params
+    Q0 = u.q0(p["J"], p["U"], d.rate)
+    K = d.rate * u.K1
+    spp = stable_spp_estimate(d)
+    h = 2 * np.pi / p["omega"] / spp
+    eps = OP.eps_fn(p["E"], p["A"], p["omega"])
+    v = SYS.initial_v(d)
+    sample = 8   # RK4 steps per bench step of the reference arm (bounded sample)
+    for _ in range(args.warmup):
+        v, _ = OP.rk4(Q0, u.Q1, K, eps, v, h, sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, _ = OP.rk4(Q0, u.Q1, K, eps, v, h, sample)
+    el = time.perf_counter() - t0
+    val = args.steps * sample / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "driven Bose dimer N=1000 (D=999999), FP64 RK4 at the stable step", "N": N_BENCH,
+                       "rk4_steps_per_bench_step": sample, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} RK4 steps per bench step (scipy CSR SpMV, single thread); "
+                                       f"oracle assembly {asm_s:.1f} s untimed"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "oracle_assembly_s": asm_s}
+    print(json.dumps(line), flush=True)
+
+
+def stable_spp_estimate(d):
+    """Host-only copy of the library's stability bound (used only by the reference arm)."""
+    H = (d.params["J"] * d.HJ.to_scipy() + d.params["U"] * d.HU.to_scipy()).toarray()
+    H1 = np.diag(d.H1.to_scipy().diagonal().real)
+    spread = 0.0
+    for e in (d.params["E"] - d.params["A"], d.params["E"] + d.params["A"]):
+        M = H + e * H1
+        c = np.real(np.diag(M))
+        r = np.abs(M).sum(1) - np.abs(np.diag(M))
+        spread = max(spread, (c + r).max() - (c - r).min())
+    L = np.abs(d.L.to_scipy().toarray())
+    diss = 2 * d.rate * L.sum(0).max() * L.sum(1).max()
+    return int(np.ceil(2 * np.pi / d.params["omega"] * (spread + diss) / 2.6))
+
+
+# ---------------------------------------------------------------------- GPU arm
+
+def cpu_baseline_sample():
+    """The oracle as it stands on this host: assembly, then a bounded number of RK4 steps."""
+    from oracle import native, propagate as OP, system as SYS
+    from paper_1812_11626_gb300 import workloads as W
+    native.build()
+    d = W.dimer(N_BENCH)
+    t0 = time.perf_counter()
+    u = SYS.unfold_dimer(d)
+    asm_s = time.perf_counter() - t0
+    p = d.params
+    Q0 = u.q0(p["J"], p["U"], d.rate)
+    spp = stable_spp_estimate(d)
+    h = 2 * np.pi / p["omega"] / spp
+    v = SYS.initial_v(d)
+    n = 40
+    t0 = time.perf_counter()
+    OP.rk4(Q0, u.Q1, d.rate * u.K1, OP.eps_fn(p["E"], p["A"], p["omega"]), v, h, n)
+    el = time.perf_counter() - t0
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 RK4 steps of the N=1000 dimer (scipy CSR SpMV, one thread), "
+                      f"after the oracle's definition-route assembly ({asm_s:.1f} s)",
+            "assembly_s": asm_s}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1812_11626_gb300 import gksl as G
+    from paper_1812_11626_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.Stream()
+    d = W.dimer(N_BENCH)
+    ctx = G.dimer_context(d, device=local, stream=stream.cuda_stream, flags=G.GKSL_ASM_FP32, assemble=False)
+    asm_s = G.gksl_assemble(ctx, G.GKSL_ASM_FP32)
+    G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+    info = G.gksl_get_info(ctx)
+    D = info.D
+    spp = G.gksl_min_stable_steps(ctx)
+
+    def step(prec=64):
+        G.gksl_propagate(ctx, spp, STEP_RK4, prec, 0, 0, None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_all = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = world * args.steps * STEP_RK4 / (ms_all * 1e-3)
+    avg_launch_ms = ms / (args.steps * STEP_RK4 * 4)
+    bytes_launch = stage_bytes(info.nnz_q0, info.nnz_q1, D, 64)
+    hbm, peak_kind = peaks()
+    achieved = bytes_launch / (avg_launch_ms * 1e-3) / 1e9
+    traffic = None
+    if os.path.exists(PROFILE_JSON):
+        pj = json.load(open(PROFILE_JSON))
+        if pj.get("src_hash") == src_hash():
+            traffic = pj.get("dram_bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch,
+                "kernel": "k_stage64<*,18> (fused SpMV + RK4 stage update)"}
+
+    # end to end through the C ABI with pinned host buffers: H2D of v, propagate, D2H of v
+    host_in = torch.empty(D, dtype=torch.float64, pin_memory=True)
+    host_out = torch.empty(D, dtype=torch.float64, pin_memory=True)
+    G.gksl_get_state(ctx, host_in.numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        G.gksl_set_state(ctx, host_in, 0.0)
+        G.gksl_propagate(ctx, spp, STEP_RK4, 64, 0, STEP_RK4, host_out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * args.steps * STEP_RK4 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * D,
+           "d2h_bytes_per_step": 8 * D}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # FP32 bulk form on the same workload
+        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+        G.gksl_propagate(ctx, spp, STEP_RK4, 32, 0, 0, None)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            G.gksl_propagate(ctx, spp, STEP_RK4, 32, 0, 0, None)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = f0.elapsed_time(f1)
+        b32 = stage_bytes(info.nnz_q0, info.nnz_q1, D, 32)
+        extras["fp32_bulk"] = {"value": args.steps * STEP_RK4 / (ms32 * 1e-3), "unit": UNIT,
+                               "achieved_gbs": b32 / (ms32 * 1e-3 / (args.steps * STEP_RK4 * 4)) / 1e9}
+        extras["assembly_s"] = asm_s
+        extras["nnz_q0"] = info.nnz_q0
+        extras["device_bytes"] = info.device_bytes
+        extras["spmv_hbm_gbs"] = achieved
+        extras["steps_per_period_stable"] = spp
+    G.gksl_destroy(ctx)
+    if not args.no_extras and rank == 0:
+        extras.update(batched_and_adjoint(G, W, torch))
+
+    if rank == 0:
+        cpu = cpu_baseline_sample()
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "driven Bose dimer N=1000 (D=999999), FP64 RK4 at the stable step size",
+                           "N": N_BENCH, "rk4_steps_per_bench_step": STEP_RK4, "steps_per_period": spp,
+                           "l2": "inputs larger than L2 (Q0 stream 233 MB > 129 MB)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": {k: v for k, v in cpu.items() if k != "assembly_s"},
+                "e2e": e2e, "gpu_launches": args.steps * launches_per_call(STEP_RK4), "clocks": ck,
+                "extras": extras}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def batched_and_adjoint(G, W, torch):
+    """Side measurements: the batched form (256 seeded instances, N in {50, 100, 200}) and the
+    adjoint gradient at N = 200, each against the plain FP64 single-instance path."""
+    out = {}
+    inst = W.batch_instances(256, 1812)
+    groups = {}
+    for i in inst:
+        groups.setdefault(i["N"], []).append(i)
+    ctxs, n_inst, A, g, spps = [], [], [], [], []
+    for N in sorted(groups):
+        d = W.dimer(N)
+        d.rate = 1.0 / (N - 1)
+        c = G.dimer_context(d, flags=G.GKSL_ASM_FP32)
+        ctxs.append(c)
+        n_inst.append(len(groups[N]))
+        A += [x["A"] for x in groups[N]]
+        g += [x["gamma"] for x in groups[N]]
+        # stable step count for the largest A and gamma of the group
+        G.gksl_set_drive(c, d.params["E"], max(x["A"] for x in groups[N]), d.params["omega"])
+        G.gksl_set_gamma(c, 0, max(x["gamma"] for x in groups[N]) / (N - 1))
+        spps.append(G.gksl_min_stable_steps(c))
+        G.gksl_set_gamma(c, 0, 1.0 / (N - 1))
+        G.gksl_set_drive(c, d.params["E"], d.params["A"], d.params["omega"])
+    b = G.gksl_batch_create(ctxs, n_inst, A, g)
+    # a tenth of a period per group at its stable step size (the per-step cost is what is timed)
+    steps = [max(1, s // 10) for s in spps]
+    G.gksl_batch_propagate(b, steps, 1, 0)   # warm-up, includes the tile autotuning
+    G.gksl_batch_reset(b)
+    sec = G.gksl_batch_propagate(b, steps, 1, 0)
+    inst_steps = sum(n * s for n, s in zip(n_inst, steps))
+    tiles = [G.gksl_batch_info(b, i) for i in range(len(ctxs))]
+    G.gksl_batch_destroy(b)
+    # plain FP64 single-instance path on the same groups for comparison
+    plain = 0.0
+    for c, s in zip(ctxs, steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.gksl_propagate(c, s, min(s, 2000), 64, 0, 0, None)
+        torch.cuda.synchronize()
+        plain += (time.perf_counter() - t0) / min(s, 2000)
+    for c in ctxs:
+        G.gksl_destroy(c)
+    out["batched"] = {"instance_steps_per_s": inst_steps / sec, "instances": sum(n_inst),
+                      "groups": {str(N): {"instances": n, "steps": s, "instances_per_lane": t[0], "tuned_us": t[1]}
+                                 for N, n, s, t in zip(sorted(groups), n_inst, steps, tiles)},
+                      "plain_fp64_instance_steps_per_s": len(ctxs) / plain if plain > 0 else None}
+    # adjoint at N = 200: gradient of the mean of <n1 - n2> over period 1 at the stable step size
+    d = W.dimer(200)
+    c = G.dimer_context(d)
+    try:
+        S = G.gksl_min_stable_steps(c)
+        for prec in (64, 32):
+            grad = np.zeros(4)
+            t0 = time.perf_counter()
+            G.gksl_adjoint_timeavg(c, d.obs_diag, S, 1, prec, grad)
+            el = time.perf_counter() - t0
+            out[f"adjoint_fp{prec}"] = {"seconds": el, "forward_steps": S, "steps_per_s": S / el}
+        t0 = time.perf_counter()
+        G.gksl_propagate(c, S, S, 64, 0, 0, None)
+        out["adjoint_plain_fp64_steps_per_s"] = S / (time.perf_counter() - t0)
+    finally:
+        G.gksl_destroy(c)
+    return out
+
+
+if __name__ == "__main__":
+    main()

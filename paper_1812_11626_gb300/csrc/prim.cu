@@ -98,7 +98,14 @@ long long scan_impl(const TIn *in, long long *out, long long n, bool with_total,
     DBuf<long long> sums((size_t)nt), offs((size_t)nt + 1);
     k_tile_sums<TIn><<<(unsigned)nt, kT, 0, s>>>(in, n, sums.p);
     GK_LAUNCH_CHECK();
-    scan_impl<long long>(sums.p, offs.p, nt, true, false, s);
+    if (nt == 1) {
+        // one tile: its offset is 0 and the total is its sum (no further recursion)
+        k_set_ll<<<1, 1, 0, s>>>(offs.p, 0);
+        GK_LAUNCH_CHECK();
+        GK_CUDA(cudaMemcpyAsync(offs.p + 1, sums.p, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+    } else {
+        scan_impl<long long>(sums.p, offs.p, nt, true, false, s);
+    }
     k_tile_apply<TIn><<<(unsigned)nt, kT, 0, s>>>(in, out, n, offs.p);
     GK_LAUNCH_CHECK();
     if (with_total) GK_CUDA(cudaMemcpyAsync(out + n, offs.p + nt, sizeof(long long), cudaMemcpyDeviceToDevice, s));
