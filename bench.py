@@ -202,10 +202,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling case for ncu: N=1000 assembly, then 50 FP64 and 50 FP32 RK4 steps")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile:
+        run_profile_case()
         return
 
     import torch
@@ -326,6 +331,24 @@ def main():
         dist.destroy_process_group()
 
 
+def run_profile_case():
+    """Small, fixed case for ncu: the N = 1000 workload (matrix stream 233 MB > L2, about 1 GB
+    held on the device), 50 FP64 then 50 FP32 RK4 steps."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1812_11626_gb300 import gksl as G
+    from paper_1812_11626_gb300 import workloads as W
+    d = W.dimer(N_BENCH)
+    ctx = G.dimer_context(d, flags=G.GKSL_ASM_FP32)
+    spp = G.gksl_min_stable_steps(ctx)
+    G.gksl_propagate(ctx, spp, 50, 64, 0, 0, None)
+    G.gksl_propagate(ctx, spp, 50, 32, 0, 0, None)
+    info = G.gksl_get_info(ctx)
+    print(json.dumps({"profile_case": "N=1000", "nnz_q0": info.nnz_q0, "nnz_q1": info.nnz_q1, "D": info.D,
+                      "src_hash": src_hash(), "steps_per_period": spp}), flush=True)
+    G.gksl_destroy(ctx)
+
+
 def batched_and_adjoint(G, W, torch):
     """Side measurements: the batched form (256 seeded instances, N in {50, 100, 200}) and the
     adjoint gradient at N = 200, each against the plain FP64 single-instance path."""
@@ -349,29 +372,32 @@ def batched_and_adjoint(G, W, torch):
         spps.append(G.gksl_min_stable_steps(c))
         G.gksl_set_gamma(c, 0, 1.0 / (N - 1))
         G.gksl_set_drive(c, d.params["E"], d.params["A"], d.params["omega"])
+        G.gksl_assemble(c, G.GKSL_ASM_FP32)
     b = G.gksl_batch_create(ctxs, n_inst, A, g)
     # a tenth of a period per group at its stable step size (the per-step cost is what is timed)
     steps = [max(1, s // 10) for s in spps]
-    G.gksl_batch_propagate(b, steps, 1, 0)   # warm-up, includes the tile autotuning
+    G.gksl_batch_propagate(b, spps, steps, 0)   # warm-up, includes the tile autotuning
     G.gksl_batch_reset(b)
-    sec = G.gksl_batch_propagate(b, steps, 1, 0)
+    sec = G.gksl_batch_propagate(b, spps, steps, 0)
     inst_steps = sum(n * s for n, s in zip(n_inst, steps))
     tiles = [G.gksl_batch_info(b, i) for i in range(len(ctxs))]
     G.gksl_batch_destroy(b)
     # plain FP64 single-instance path on the same groups for comparison
-    plain = 0.0
-    for c, s in zip(ctxs, steps):
+    plain = 0.0   # seconds the plain path needs for the same instance-steps, run one by one
+    for c, spp_g, s, ni in zip(ctxs, spps, steps, n_inst):
+        n = min(s, 2000)
+        G.gksl_propagate(c, spp_g, 64, 64, 0, 0, None)   # warm-up (graph capture)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G.gksl_propagate(c, s, min(s, 2000), 64, 0, 0, None)
+        G.gksl_propagate(c, spp_g, n, 64, 0, 0, None)
         torch.cuda.synchronize()
-        plain += (time.perf_counter() - t0) / min(s, 2000)
+        plain += (time.perf_counter() - t0) / n * s * ni
     for c in ctxs:
         G.gksl_destroy(c)
     out["batched"] = {"instance_steps_per_s": inst_steps / sec, "instances": sum(n_inst),
                       "groups": {str(N): {"instances": n, "steps": s, "instances_per_lane": t[0], "tuned_us": t[1]}
                                  for N, n, s, t in zip(sorted(groups), n_inst, steps, tiles)},
-                      "plain_fp64_instance_steps_per_s": len(ctxs) / plain if plain > 0 else None}
+                      "plain_fp64_instance_steps_per_s": inst_steps / plain if plain > 0 else None}
     # adjoint at N = 200: gradient of the mean of <n1 - n2> over period 1 at the stable step size
     d = W.dimer(200)
     c = G.dimer_context(d)

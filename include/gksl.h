@@ -188,13 +188,16 @@ gksl_status gksl_adjoint_timeavg(gksl_ctx *ctx, const double *o_diag, long long 
 gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, const int *n_inst, const double *A,
                               const double *g, gksl_batch **out);
 void gksl_batch_destroy(gksl_batch *b);
+/* Message of the last failed call on this batch; with b == NULL, of the calling thread's last
+ * failed gksl_batch_create. */
 const char *gksl_batch_last_error(const gksl_batch *b);
 /* Reset every instance to its group's current state vector, t = 0. */
 gksl_status gksl_batch_reset(gksl_batch *b);
-/* Advance every group by `periods` periods of steps_per_period[i] steps (FP32 bulk, FP64 master
- * state, an FP64 step every correction_every steps, <= 0: never).  `seconds` (may be NULL)
- * receives the device time of the whole run. */
-gksl_status gksl_batch_propagate(gksl_batch *b, const long long *steps_per_period, long long periods,
+/* Advance group i by n_steps[i] RK4 steps of h = T / steps_per_period[i] from the batch's current
+ * time (FP32 bulk, FP64 master state, an FP64 step every correction_every steps, <= 0: never);
+ * groups with fewer steps stop early.  `seconds` (may be NULL) receives the device time of the
+ * whole run. */
+gksl_status gksl_batch_propagate(gksl_batch *b, const long long *steps_per_period, const long long *n_steps,
                                  long long correction_every, double *seconds);
 /* State of instance i (D_i doubles, FP64 master). */
 gksl_status gksl_batch_get_state(gksl_batch *b, int instance, double *v);

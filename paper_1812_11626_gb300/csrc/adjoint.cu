@@ -43,7 +43,7 @@ struct AdjArgs {
     int nkp;
     int npar;
     double alpha;   // kb = alpha * x
-    double h;
+    double h, h2, h3, h6;   // h, h/2, h/3, h/6 (computed on the host)
     double beta;    // stage 1: lam += beta * w
     const int *long_rows;
     long long n_long;
@@ -74,10 +74,9 @@ template <int STAGE, typename VT>
 __device__ inline void adj_epilogue(const AdjArgs<VT> &a, long long r, double ybar, const double *__restrict__ lam,
                                     double *__restrict__ lacc, VT *__restrict__ kb_out, const double *__restrict__ w,
                                     double *lam_out) {
-    double h = a.h;
-    if (STAGE == 4) { kb_out[r] = (VT)((h / 3.0) * lam[r] + h * ybar); lacc[r] = lam[r] + ybar; }
-    if (STAGE == 3) { kb_out[r] = (VT)((h / 3.0) * lam[r] + (0.5 * h) * ybar); lacc[r] = lacc[r] + ybar; }
-    if (STAGE == 2) { kb_out[r] = (VT)((h / 6.0) * lam[r] + (0.5 * h) * ybar); lacc[r] = lacc[r] + ybar; }
+    if (STAGE == 4) { kb_out[r] = (VT)(a.h3 * lam[r] + a.h * ybar); lacc[r] = lam[r] + ybar; }
+    if (STAGE == 3) { kb_out[r] = (VT)(a.h3 * lam[r] + a.h2 * ybar); lacc[r] = lacc[r] + ybar; }
+    if (STAGE == 2) { kb_out[r] = (VT)(a.h6 * lam[r] + a.h2 * ybar); lacc[r] = lacc[r] + ybar; }
     if (STAGE == 1) { lam_out[r] = lacc[r] + ybar + a.beta * w[r]; }
 }
 
@@ -203,6 +202,9 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
         for (int p = 0; p < GKSL_MAX_P; ++p)
             if (c->has_r[p]) { a.kp[a.nkp] = c->Kp[p].p; a.kp_gidx[a.nkp++] = slot_gamma[p]; }
         a.h = h;
+        a.h2 = 0.5 * h;
+        a.h3 = h / 3.0;
+        a.h6 = h / 6.0;
         a.long_rows = c->adj[0].long_rows.p;
         a.n_long = c->adj[0].n_long;
         a.nb_long = (int)((a.n_long + kWarps - 1) / kWarps);

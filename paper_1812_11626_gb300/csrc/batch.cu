@@ -39,9 +39,12 @@ struct GroupDev {
     long long D;
     int B, ipl, nchunks;
     long long nsteps;
-    double h;
+    double h, h2, h6;   // h, h/2, h/6 (computed on the host)
+    float hf, h2f, h6f;
     const double *sin_tab;   // sin(omega t) at the 3 stage times of each step
+    const float *sin_tab_f;  // the same in FP32 (FP32 steps use no FP64 arithmetic)
     const double *A, *g;
+    const float *Af, *gf;
     double *V64;
     float *V32, *Y32[2], *ACC32;
     double *Y64[2], *ACC64;
@@ -95,29 +98,31 @@ __global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
             }
         }
         const int slot = STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1);
-        const double sn = G.sin_tab[3 * step + slot];
-        const double h = G.h;
+        const long long ts = 3 * step + slot;
+        const double h = G.h, h2 = G.h2, h6 = G.h6;
 #pragma unroll
         for (int k = 0; k < kMaxIpl; ++k) {
             int b = b0 + 32 * k;
             if (k >= G.ipl || b >= B) continue;
             long long o = r * B + b;
-            VT kv = acc[0][k] + (VT)(G.A[b] * sn) * acc[1][k] + (VT)G.g[b] * acc[2][k];
+            VT kv;
+            if (F64) kv = (VT)(acc[0][k] + (G.A[b] * G.sin_tab[ts]) * acc[1][k] + G.g[b] * acc[2][k]);
+            else kv = (VT)(acc[0][k] + (G.Af[b] * G.sin_tab_f[ts]) * acc[1][k] + G.gf[b] * acc[2][k]);
             if (F64) {
                 double *yn = STAGE == 1 ? G.Y64[0] : (STAGE == 2 ? G.Y64[1] : G.Y64[0]);
                 double kd = (double)kv;
-                if (STAGE == 1) { yn[o] = G.V64[o] + (0.5 * h) * kd; G.ACC64[o] = kd; }
-                if (STAGE == 2) { yn[o] = G.V64[o] + (0.5 * h) * kd; G.ACC64[o] += 2.0 * kd; }
+                if (STAGE == 1) { yn[o] = G.V64[o] + h2 * kd; G.ACC64[o] = kd; }
+                if (STAGE == 2) { yn[o] = G.V64[o] + h2 * kd; G.ACC64[o] += 2.0 * kd; }
                 if (STAGE == 3) { yn[o] = G.V64[o] + h * kd; G.ACC64[o] += 2.0 * kd; }
-                if (STAGE == 4) { G.V64[o] = G.V64[o] + (h / 6.0) * (G.ACC64[o] + kd); G.V32[o] = (float)G.V64[o]; }
+                if (STAGE == 4) { G.V64[o] = G.V64[o] + h6 * (G.ACC64[o] + kd); G.V32[o] = (float)G.V64[o]; }
             } else {
                 float *yn = STAGE == 1 ? G.Y32[0] : (STAGE == 2 ? G.Y32[1] : G.Y32[0]);
-                float kf = (float)kv, hf = (float)h;
-                if (STAGE == 1) { yn[o] = G.V32[o] + (0.5f * hf) * kf; G.ACC32[o] = kf; }
-                if (STAGE == 2) { yn[o] = G.V32[o] + (0.5f * hf) * kf; G.ACC32[o] += 2.0f * kf; }
+                float kf = (float)kv, hf = G.hf, h2f = G.h2f, h6f = G.h6f;
+                if (STAGE == 1) { yn[o] = G.V32[o] + h2f * kf; G.ACC32[o] = kf; }
+                if (STAGE == 2) { yn[o] = G.V32[o] + h2f * kf; G.ACC32[o] += 2.0f * kf; }
                 if (STAGE == 3) { yn[o] = G.V32[o] + hf * kf; G.ACC32[o] += 2.0f * kf; }
                 if (STAGE == 4) {
-                    float inc = (float)(h / 6.0) * (G.ACC32[o] + kf);
+                    float inc = h6f * (G.ACC32[o] + kf);
                     double nv = G.V64[o] + (double)inc;
                     G.V64[o] = nv;
                     G.V32[o] = (float)nv;
@@ -127,13 +132,18 @@ __global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
     }
 }
 
-__global__ void k_sin_table(double t0, double h, double omega, long long n, double *__restrict__ tab) {
+__global__ void k_sin_table(double t0, double h, double omega, long long n, double *__restrict__ tab,
+                            float *__restrict__ tabf) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double tn = t0 + (double)i * h;
-    tab[3 * i + 0] = sin(omega * tn);
-    tab[3 * i + 1] = sin(omega * (tn + 0.5 * h));
-    tab[3 * i + 2] = sin(omega * (tn + h));
+    double s0 = sin(omega * tn), s1 = sin(omega * (tn + 0.5 * h)), s2 = sin(omega * (tn + h));
+    tab[3 * i + 0] = s0;
+    tab[3 * i + 1] = s1;
+    tab[3 * i + 2] = s2;
+    tabf[3 * i + 0] = (float)s0;
+    tabf[3 * i + 1] = (float)s1;
+    tabf[3 * i + 2] = (float)s2;
 }
 
 __global__ void k_replicate(const double *__restrict__ v, long long rows, int B, double *__restrict__ V64,
@@ -178,9 +188,11 @@ struct Group {
     CsrR m[3];            // QH (E folded), Q1, [R | K]
     DBuf<float> mf[3];    // FP32 values
     DBuf<double> A, g, V64, Y64a, Y64b, ACC64, sin_tab;
+    DBuf<float> Af, gf, sin_tab_f;
     DBuf<float> V32, Ya, Yb, ACC32;
     long long nsteps = 0;
     double h = 0.0;
+    double t = 0.0;   // time of the group's states
     double tuned_us = 0.0;
 };
 
@@ -234,9 +246,17 @@ BatchArgs make_args(gksl_batch *b, long long local) {
         d.nchunks = (G.B + 32 * G.ipl - 1) / (32 * G.ipl);
         d.nsteps = G.nsteps;
         d.h = G.h;
+        d.h2 = 0.5 * G.h;
+        d.h6 = G.h / 6.0;
+        d.hf = (float)G.h;
+        d.h2f = (float)(0.5 * G.h);
+        d.h6f = (float)(G.h / 6.0);
         d.sin_tab = G.sin_tab.p;
+        d.sin_tab_f = G.sin_tab_f.p;
         d.A = G.A.p;
         d.g = G.g.p;
+        d.Af = G.Af.p;
+        d.gf = G.gf.p;
         d.V64 = G.V64.p;
         d.V32 = G.V32.p;
         d.Y32[0] = G.Ya.p;
@@ -320,6 +340,7 @@ void reset_batch(gksl_batch *b) {
     for (auto &G : b->groups) {
         gksl_ctx *c = G.ctx;
         GK_REQUIRE(c->state_set, GKSL_ERR_STATE, "a group context has no state");
+        G.t = 0.0;
         long long rows = G.D + 1;
         k_replicate<<<grid_for(rows * G.B, 256), 256, 0, b->stream>>>(c->v.p, rows, G.B, G.V64.p, G.V32.p);
         GK_LAUNCH_CHECK();
@@ -343,8 +364,11 @@ void autotune(gksl_batch *b) {
         for (auto *H : all) saved.push_back(H->nsteps);
         for (auto *H : all) H->nsteps = (H == G) ? 1LL << 40 : 0;
         std::vector<double> tab_saved;
-        if (G->sin_tab.n < 3 * 64) G->sin_tab.alloc(3 * 64);
-        k_sin_table<<<1, 64, 0, b->stream>>>(0.0, 1e-6, 1.0, 16, G->sin_tab.p);
+        if (G->sin_tab.n < 3 * 64) {
+            G->sin_tab.alloc(3 * 64);
+            G->sin_tab_f.alloc(3 * 64);
+        }
+        k_sin_table<<<1, 64, 0, b->stream>>>(0.0, 1e-6, 1.0, 16, G->sin_tab.p, G->sin_tab_f.p);
         GK_LAUNCH_CHECK();
         double best = 1e300;
         int best_ipl = 1;
@@ -398,6 +422,8 @@ gksl_status bguarded(gksl_batch *b, F &&f) {
     }
 }
 }  // namespace
+
+static thread_local std::string g_create_error;
 
 extern "C" gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, const int *n_inst, const double *A,
                                          const double *g, gksl_batch **out) {
@@ -497,8 +523,13 @@ extern "C" gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, 
             GK_CUDA(cudaStreamSynchronize(s));
             G.A.alloc((size_t)G.B);
             G.g.alloc((size_t)G.B);
+            G.Af.alloc((size_t)G.B);
+            G.gf.alloc((size_t)G.B);
             GK_CUDA(cudaMemcpy(G.A.p, hA.data() + off, sizeof(double) * G.B, cudaMemcpyHostToDevice));
             GK_CUDA(cudaMemcpy(G.g.p, hg.data() + off, sizeof(double) * G.B, cudaMemcpyHostToDevice));
+            std::vector<float> fa(hA.begin() + off, hA.begin() + off + G.B), fg(hg.begin() + off, hg.begin() + off + G.B);
+            GK_CUDA(cudaMemcpy(G.Af.p, fa.data(), sizeof(float) * G.B, cudaMemcpyHostToDevice));
+            GK_CUDA(cudaMemcpy(G.gf.p, fg.data(), sizeof(float) * G.B, cudaMemcpyHostToDevice));
             long long n = (G.D + 1) * G.B;
             G.V64.alloc((size_t)n);
             G.Y64a.alloc((size_t)n);
@@ -514,9 +545,11 @@ extern "C" gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, 
         reset_batch(b);
     });
     if (st != GKSL_OK) {
+        g_create_error = b->err;
         delete b;
         return st;
     }
+    g_create_error.clear();
     *out = b;
     return GKSL_OK;
 }
@@ -528,35 +561,40 @@ extern "C" void gksl_batch_destroy(gksl_batch *b) {
     delete b;
 }
 
-extern "C" const char *gksl_batch_last_error(const gksl_batch *b) { return b ? b->err.c_str() : "null batch"; }
+extern "C" const char *gksl_batch_last_error(const gksl_batch *b) {
+    return b ? b->err.c_str() : g_create_error.c_str();
+}
 
 extern "C" gksl_status gksl_batch_reset(gksl_batch *b) {
     return bguarded(b, [&] { reset_batch(b); });
 }
 
-extern "C" gksl_status gksl_batch_propagate(gksl_batch *b, const long long *spp, long long periods,
+extern "C" gksl_status gksl_batch_propagate(gksl_batch *b, const long long *spp, const long long *n_steps,
                                             long long correction_every, double *seconds) {
     return bguarded(b, [&] {
-        GK_REQUIRE(spp && periods >= 0, GKSL_ERR_ARG, "steps_per_period array required, periods >= 0");
+        GK_REQUIRE(spp && n_steps, GKSL_ERR_ARG, "steps_per_period and n_steps arrays required");
         if (!b->tuned) autotune(b);
         long long maxsteps = 0;
         for (size_t i = 0; i < b->groups.size(); ++i) {
             Group &G = b->groups[i];
-            GK_REQUIRE(spp[i] > 0, GKSL_ERR_ARG, "steps_per_period must be > 0");
+            GK_REQUIRE(spp[i] > 0 && n_steps[i] >= 0, GKSL_ERR_ARG, "steps_per_period > 0 and n_steps >= 0 required");
             double T = 2.0 * M_PI / G.ctx->omega;
             double h = T / (double)spp[i];
-            long long n = spp[i] * periods;
+            long long n = n_steps[i];
             if (G.h != h || G.nsteps != n) clear_batch_graphs(b);
             G.h = h;
             G.nsteps = n;
             if (G.sin_tab.n < (size_t)(3 * std::max(1LL, n))) {
                 G.sin_tab.alloc((size_t)(3 * std::max(1LL, n)));
+                G.sin_tab_f.alloc((size_t)(3 * std::max(1LL, n)));
                 clear_batch_graphs(b);
             }
             if (n > 0) {
-                k_sin_table<<<grid_for(n, 256), 256, 0, b->stream>>>(0.0, h, G.ctx->omega, n, G.sin_tab.p);
+                k_sin_table<<<grid_for(n, 256), 256, 0, b->stream>>>(G.t, h, G.ctx->omega, n, G.sin_tab.p,
+                                                                     G.sin_tab_f.p);
                 GK_LAUNCH_CHECK();
             }
+            G.t += (double)n * h;
             maxsteps = std::max(maxsteps, n);
         }
         cudaEvent_t e0, e1;

@@ -84,26 +84,31 @@ __device__ inline AT tail_dot(const HybView<VT> &H, long long i, int lane, const
 template <int STAGE>
 __device__ inline int eps_slot() { return STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1); }
 
+// step-size constants, computed once on the host (no per-thread FP64 division)
+struct HConst {
+    double h, h2, h6;   // h, h/2, h/6
+    float hf, h2f, h6f;
+};
+
 // ---- FP64 epilogue
 template <int STAGE>
 __device__ inline void epi64(long long r, double k, double *v, double *__restrict__ yn, double *__restrict__ acc,
-                             double h) {
-    if (STAGE == 1) { yn[r] = v[r] + (0.5 * h) * k; acc[r] = k; }
-    if (STAGE == 2) { yn[r] = v[r] + (0.5 * h) * k; acc[r] = acc[r] + 2.0 * k; }
-    if (STAGE == 3) { yn[r] = v[r] + h * k; acc[r] = acc[r] + 2.0 * k; }
-    if (STAGE == 4) { v[r] = v[r] + (h / 6.0) * (acc[r] + k); }
+                             const HConst &c) {
+    if (STAGE == 1) { yn[r] = v[r] + c.h2 * k; acc[r] = k; }
+    if (STAGE == 2) { yn[r] = v[r] + c.h2 * k; acc[r] = acc[r] + 2.0 * k; }
+    if (STAGE == 3) { yn[r] = v[r] + c.h * k; acc[r] = acc[r] + 2.0 * k; }
+    if (STAGE == 4) { v[r] = v[r] + c.h6 * (acc[r] + k); }
 }
 
 // ---- FP32 epilogue (v32: FP32 mirror, v64: master)
 template <int STAGE>
 __device__ inline void epi32(long long r, float k, float *v32, double *v64, float *__restrict__ yn,
-                             float *__restrict__ acc, double h) {
-    float hf = (float)h;
-    if (STAGE == 1) { yn[r] = v32[r] + (0.5f * hf) * k; acc[r] = k; }
-    if (STAGE == 2) { yn[r] = v32[r] + (0.5f * hf) * k; acc[r] = acc[r] + 2.0f * k; }
-    if (STAGE == 3) { yn[r] = v32[r] + hf * k; acc[r] = acc[r] + 2.0f * k; }
+                             float *__restrict__ acc, const HConst &c) {
+    if (STAGE == 1) { yn[r] = v32[r] + c.h2f * k; acc[r] = k; }
+    if (STAGE == 2) { yn[r] = v32[r] + c.h2f * k; acc[r] = acc[r] + 2.0f * k; }
+    if (STAGE == 3) { yn[r] = v32[r] + c.hf * k; acc[r] = acc[r] + 2.0f * k; }
     if (STAGE == 4) {
-        float inc = (float)(h / 6.0) * (acc[r] + k);
+        float inc = c.h6f * (acc[r] + k);
         double nv = v64[r] + (double)inc;
         v64[r] = nv;
         v32[r] = (float)nv;
@@ -118,7 +123,7 @@ struct StepArgs {
     const double *eps_tab;
     const long long *base;
     long long local;
-    double h;
+    HConst hc;
 };
 
 template <int STAGE, int W>
@@ -135,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) k_stage64(HybView<double> A0, HybVie
         if (i >= a.n_long) return;
         double s0 = tail_dot<double, double>(A0, i, lane, y);
         double s1 = tail_dot<double, double>(A1, i, lane, y);
-        if (lane == 0) epi64<STAGE>(a.long_rows[i], s0 + eps * s1, v, yn, acc, a.h);
+        if (lane == 0) epi64<STAGE>(a.long_rows[i], s0 + eps * s1, v, yn, acc, a.hc);
         return;
     }
     long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
@@ -145,7 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_stage64(HybView<double> A0, HybVie
     double a0 = ldcs(A0.ell_val + r);
     double s0 = ell_dot<double, double, W>(A0, r, c0, a0, y);
     double s1 = ell_dot_full<double, double>(A1, r, y);
-    epi64<STAGE>(r, s0 + eps * s1, v, yn, acc, a.h);
+    epi64<STAGE>(r, s0 + eps * s1, v, yn, acc, a.hc);
 }
 
 template <int STAGE, int W>
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_stage32(HybView<float> A0, HybView
         if (i >= a.n_long) return;
         float s0 = tail_dot<float, float>(A0, i, lane, y);
         float s1 = tail_dot<float, float>(A1, i, lane, y);
-        if (lane == 0) epi32<STAGE>(a.long_rows[i], s0 + eps * s1, v32, v64, yn, acc, a.h);
+        if (lane == 0) epi32<STAGE>(a.long_rows[i], s0 + eps * s1, v32, v64, yn, acc, a.hc);
         return;
     }
     long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) k_stage32(HybView<float> A0, HybView
     float a0 = ldcs(A0.ell_val + r);
     float s0 = ell_dot<float, float, W>(A0, r, c0, a0, y);
     float s1 = ell_dot_full<float, float>(A1, r, y);
-    epi32<STAGE>(r, s0 + eps * s1, v32, v64, yn, acc, a.h);
+    epi32<STAGE>(r, s0 + eps * s1, v32, v64, yn, acc, a.hc);
 }
 
 __global__ void k_to_f32(const double *__restrict__ v, float *__restrict__ o, long long n) {
@@ -209,7 +214,12 @@ Launch make_launch(gksl_ctx *c, const Hyb<double> &h0, double h, const double *t
     L.a.eps_tab = tab;
     L.a.base = c->step_base.p;
     L.a.local = local;
-    L.a.h = h;
+    L.a.hc.h = h;
+    L.a.hc.h2 = 0.5 * h;
+    L.a.hc.h6 = h / 6.0;
+    L.a.hc.hf = (float)h;
+    L.a.hc.h2f = 0.5f * (float)h;
+    L.a.hc.h6f = (float)(h / 6.0);
     L.grid = (unsigned)(L.a.nb_long + (c->D + kThreads - 1) / kThreads);
     return L;
 }

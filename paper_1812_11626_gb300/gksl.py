@@ -79,7 +79,7 @@ _SIGS = {
     "gksl_batch_destroy": (None, [_P]),
     "gksl_batch_last_error": (ctypes.c_char_p, [_P]),
     "gksl_batch_reset": (_S, [_P]),
-    "gksl_batch_propagate": (_S, [_P, _P, _L, _L, ctypes.POINTER(_D)]),
+    "gksl_batch_propagate": (_S, [_P, _P, _P, _L, ctypes.POINTER(_D)]),
     "gksl_batch_get_state": (_S, [_P, _I, _P]),
     "gksl_batch_info": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "gksl_get_info": (_S, [_P, ctypes.POINTER(gksl_info)]),
@@ -112,12 +112,12 @@ def _arr(x, dtype):
     return np.ascontiguousarray(x, dtype=dtype)
 
 
-def _check(st, ctx=None, batch=None):
+def _check(st, ctx=None, batch=None, batch_create=False):
     if st != GKSL_OK:
         msg = ""
         if ctx is not None:
             msg = _lib.gksl_last_error(ctx).decode()
-        elif batch is not None:
+        elif batch is not None or batch_create:
             msg = _lib.gksl_batch_last_error(batch).decode()
         raise GkslError(st, msg)
 
@@ -257,7 +257,8 @@ def gksl_batch_create(groups, n_inst, A, g):
     A = np.ascontiguousarray(A, dtype=np.float64)
     g = np.ascontiguousarray(g, dtype=np.float64)
     out = _P()
-    _check(_lib.gksl_batch_create(len(groups), ctypes.cast(arr, _P), _ptr(ni), _ptr(A), _ptr(g), ctypes.byref(out)))
+    _check(_lib.gksl_batch_create(len(groups), ctypes.cast(arr, _P), _ptr(ni), _ptr(A), _ptr(g), ctypes.byref(out)),
+           batch_create=True)
     return out.value
 
 
@@ -269,10 +270,11 @@ def gksl_batch_reset(b):
     _check(_lib.gksl_batch_reset(b), batch=b)
 
 
-def gksl_batch_propagate(b, steps_per_period, periods, correction_every=0):
+def gksl_batch_propagate(b, steps_per_period, n_steps, correction_every=0):
     spp = np.ascontiguousarray(steps_per_period, dtype=np.int64)
+    ns = np.ascontiguousarray(n_steps, dtype=np.int64)
     sec = _D()
-    _check(_lib.gksl_batch_propagate(b, _ptr(spp), int(periods), int(correction_every), ctypes.byref(sec)), batch=b)
+    _check(_lib.gksl_batch_propagate(b, _ptr(spp), _ptr(ns), int(correction_every), ctypes.byref(sec)), batch=b)
     return sec.value
 
 

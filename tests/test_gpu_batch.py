@@ -32,7 +32,7 @@ def test_batch_mixed_n_vs_oracle(G):
     b = G.gksl_batch_create(ctxs, [B for _, B in sizes], A, g)
     try:
         spp, periods = 3000, 2   # above the RK4 stability bound of every instance
-        G.gksl_batch_propagate(b, [spp] * len(sizes), periods, spp)
+        G.gksl_batch_propagate(b, [spp] * len(sizes), [spp * periods] * len(sizes), spp)
         for i in list(range(0, len(inst), 7)) + [len(inst) - 1]:
             N, a, gam = inst[i]
             d = W.dimer(N, dict(A=a, gamma=gam))
@@ -57,7 +57,7 @@ def test_batch_fp64_correction_only_matches_fp64(G):
     try:
         b = G.gksl_batch_create([ctx], [2], [d.params["A"], 0.3], [1.0, 0.5])
         try:
-            G.gksl_batch_propagate(b, [400], 1, 1)
+            G.gksl_batch_propagate(b, [400], [400], 1)
             u = SYS.unfold_dimer(d)
             v_ref, _ = SYS.propagate_dimer(d, u, 400, 400)
             v = np.zeros(48)
