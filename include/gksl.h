@@ -206,6 +206,31 @@ gksl_status gksl_batch_get_state(gksl_batch *b, int instance, double *v);
  * Both are 0 before the first gksl_batch_propagate. */
 gksl_status gksl_batch_info(gksl_batch *b, int group, int *instances_per_lane, double *tuned_us_per_step);
 
+/* ------------------------------------------------------------------ allocation-free propagation */
+
+/* Largest D accepted by gksl_propagate_csr_noalloc (N <= 512). */
+#define GKSL_NOALLOC_MAX_D 262144
+
+/* The paper has no counterpart to this call; it exists for callers that cannot let a library
+ * allocate device memory (a service whose memory pool owns the whole GPU, or a loop that must
+ * not stall the device the way cudaMalloc/cudaFree can).
+ * Advances v by n_steps classical RK4 steps of dv/dt = (A0 + eps(t) A1) v + K from time t0 with
+ * step h, eps(t) = E + A sin(omega t), stage times t_n, t_n + h/2 (twice), t_n + h -- the same
+ * map as gksl_propagate.  A0 and A1 are D x D CSR matrices (int32 rowptr of D+1, int32 col,
+ * float64 val) in DEVICE memory; A1 may be NULL (all three a1 pointers), K may be NULL; v (D
+ * float64, device) is updated in place.  Everything is caller-owned and nothing is copied or
+ * allocated: the RK4 work vectors live in a fixed array compiled into the library (3 x
+ * GKSL_NOALLOC_MAX_D float64 per GPU, held until the process exits).  The first call on each
+ * device looks the array's address up (cudaGetSymbolAddress) with that device current, so make
+ * the first call before any stream capture.  Calls whose work overlaps on the GPU share the
+ * array and race.  Returns GKSL_ERR_ARG for D > GKSL_NOALLOC_MAX_D or a null pointer,
+ * GKSL_ERR_CUDA if a launch fails; work is enqueued on cuda_stream (NULL: legacy default stream)
+ * and the call does not synchronise. */
+gksl_status gksl_propagate_csr_noalloc(long long D, const int *a0_rowptr, const int *a0_col, const double *a0_val,
+                                       const int *a1_rowptr, const int *a1_col, const double *a1_val,
+                                       const double *K, double *v, double t0, double h, long long n_steps, double E,
+                                       double A, double omega, void *cuda_stream);
+
 /* ------------------------------------------------------------------ introspection */
 
 typedef struct {

@@ -83,6 +83,7 @@ _SIGS = {
     "gksl_batch_get_state": (_S, [_P, _I, _P]),
     "gksl_batch_info": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "gksl_get_info": (_S, [_P, ctypes.POINTER(gksl_info)]),
+    "gksl_propagate_csr_noalloc": (_S, [_L, _P, _P, _P, _P, _P, _P, _P, _P, _D, _D, _L, _D, _D, _D, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -292,6 +293,19 @@ def gksl_get_info(ctx):
     info = gksl_info()
     _check(_lib.gksl_get_info(ctx, ctypes.byref(info)), ctx)
     return info
+
+
+GKSL_NOALLOC_MAX_D = 262144
+
+
+def gksl_propagate_csr_noalloc(D, a0_rowptr, a0_col, a0_val, a1_rowptr, a1_col, a1_val, K, v, t0, h, n_steps, E, A,
+                               omega, cuda_stream=None):
+    """Allocation-free RK4 on caller-owned device arrays (all array arguments are CUDA tensors)."""
+    st = _lib.gksl_propagate_csr_noalloc(int(D), _ptr(a0_rowptr), _ptr(a0_col), _ptr(a0_val), _ptr(a1_rowptr),
+                                         _ptr(a1_col), _ptr(a1_val), _ptr(K), _ptr(v), float(t0), float(h),
+                                         int(n_steps), float(E), float(A), float(omega), cuda_stream)
+    if st != GKSL_OK:
+        raise GkslError(st, "gksl_propagate_csr_noalloc failed (argument out of range or CUDA error)")
 
 
 # ------------------------------------------------------------------ conveniences over the calls
