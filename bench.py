@@ -310,6 +310,10 @@ def main():
         extras["device_bytes"] = info.device_bytes
         extras["spmv_hbm_gbs"] = achieved
         extras["steps_per_period_stable"] = spp
+        tinfo = G.gksl_get_info(ctx)
+        extras["stage_kernel_variant"] = {
+            p: {"chosen": tinfo.rk4_variant[i], "timed_us_per_step": [round(x, 2) for x in tinfo.rk4_variant_us[i]]}
+            for i, p in enumerate(("fp64", "fp32"))}
     G.gksl_destroy(ctx)
     if not args.no_extras and rank == 0:
         extras.update(batched_and_adjoint(G, W, torch))

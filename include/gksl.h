@@ -245,6 +245,8 @@ typedef struct {
     long long device_bytes;    /* device memory held by the context */
     double assemble_seconds;
     double max_abs_q0;
+    int rk4_variant[2];           /* stage-kernel variant in use, [0]: FP64, [1]: FP32 (chosen by timing) */
+    double rk4_variant_us[2][3];  /* timed cost per RK4 step of each variant, microseconds (0: not timed) */
 } gksl_info;
 
 gksl_status gksl_get_info(gksl_ctx *ctx, gksl_info *out);

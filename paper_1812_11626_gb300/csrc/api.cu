@@ -537,5 +537,9 @@ extern "C" gksl_status gksl_get_info(gksl_ctx *c, gksl_info *out) {
         out->device_bytes = (long long)b;
         out->assemble_seconds = c->assemble_seconds;
         out->max_abs_q0 = c->max_abs_q0;
+        for (int p = 0; p < 2; ++p) {
+            out->rk4_variant[p] = c->rk4_var[p];
+            for (int v = 0; v < 3; ++v) out->rk4_variant_us[p][v] = c->rk4_var_us[p][v];
+        }
     });
 }

@@ -599,6 +599,7 @@ void assemble(gksl_ctx *c, unsigned flags) {
     }
     c->asm_flags = flags;
     c->assembled = true;
+    c->rk4_tuned[0] = c->rk4_tuned[1] = false;   // a new matrix: time the stage-kernel variants again
     clear_graphs(c);
     GK_CUDA(cudaStreamSynchronize(s));
     c->assemble_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -83,10 +83,34 @@ __global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
 #pragma unroll
             for (int k = 0; k < kMaxIpl; ++k) acc[c][k] = VT(0);
         const int b0 = ch * 32 * G.ipl + lane;
+        // entries in groups of 4: load their columns and values, then issue every gather of the
+        // group before the products, so each warp keeps several loads in flight
+        constexpr int U = 4;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int e1 = G.ptr[c][r + 1];
-            for (int e = G.ptr[c][r]; e < e1; ++e) {
+            int e = G.ptr[c][r];
+            for (; e + U <= e1; e += U) {
+                int col[U];
+                VT v[U], x[U][kMaxIpl];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    col[u] = G.col[c][e + u];
+                    v[u] = F64 ? (VT)G.vd[c][e + u] : (VT)G.vf[c][e + u];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int k = 0; k < kMaxIpl; ++k) {
+                        int b = b0 + 32 * k;
+                        x[u][k] = (k < G.ipl && b < B) ? __ldg(X + (long long)col[u] * B + b) : VT(0);
+                    }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int k = 0; k < kMaxIpl; ++k) acc[c][k] += v[u] * x[u][k];
+            }
+            for (; e < e1; ++e) {
                 const int col = G.col[c][e];
                 const VT v = F64 ? (VT)G.vd[c][e] : (VT)G.vf[c][e];
                 const VT *xr = X + (long long)col * B;

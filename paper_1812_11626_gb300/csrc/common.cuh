@@ -196,12 +196,17 @@ struct gksl_ctx {
     gk::DBuf<long long> step_base;   // device-side step counter base for graph replays
     gk::DBuf<double> eps_tab;        // eps(t) - E at the three stage times of every step of a run
     gk::DBuf<int> flag;              // device-side status flags (non-finite state)
+    // stage-kernel variant per precision (index 0: FP64, 1: FP32), chosen by timing
+    int rk4_var[2] = {0, 0};
+    bool rk4_tuned[2] = {false, false};
+    double rk4_var_us[2][3] = {};
     // cached CUDA graphs for chunks of steps
     struct Graph {
         long long steps = 0;
         int precision = 0;
         double h = 0.0;
         cudaGraphExec_t exec = nullptr;
+        int variant = 0;
     };
     std::vector<Graph> graphs;
 };

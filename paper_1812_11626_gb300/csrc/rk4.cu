@@ -180,6 +180,127 @@ __global__ void __launch_bounds__(kThreads) k_stage32(HybView<float> A0, HybView
     epi32<STAGE>(r, s0 + eps * s1, v32, v64, yn, acc, a.hc);
 }
 
+// ---- variants of the ELL part (same arithmetic, same summation order per row)
+
+template <typename VT>
+struct Vec2;
+template <>
+struct Vec2<double> { using T = double2; };
+template <>
+struct Vec2<float> { using T = float2; };
+
+template <int STAGE, typename VT>
+__device__ inline void epi(long long r, VT k, VT *v, double *v64, VT *__restrict__ yn, VT *__restrict__ acc,
+                           const HConst &hc);
+template <>
+__device__ inline void epi<1, double>(long long r, double k, double *v, double *, double *yn, double *acc,
+                                      const HConst &hc) { epi64<1>(r, k, v, yn, acc, hc); }
+template <>
+__device__ inline void epi<2, double>(long long r, double k, double *v, double *, double *yn, double *acc,
+                                      const HConst &hc) { epi64<2>(r, k, v, yn, acc, hc); }
+template <>
+__device__ inline void epi<3, double>(long long r, double k, double *v, double *, double *yn, double *acc,
+                                      const HConst &hc) { epi64<3>(r, k, v, yn, acc, hc); }
+template <>
+__device__ inline void epi<4, double>(long long r, double k, double *v, double *, double *yn, double *acc,
+                                      const HConst &hc) { epi64<4>(r, k, v, yn, acc, hc); }
+template <>
+__device__ inline void epi<1, float>(long long r, float k, float *v, double *v64, float *yn, float *acc,
+                                     const HConst &hc) { epi32<1>(r, k, v, v64, yn, acc, hc); }
+template <>
+__device__ inline void epi<2, float>(long long r, float k, float *v, double *v64, float *yn, float *acc,
+                                     const HConst &hc) { epi32<2>(r, k, v, v64, yn, acc, hc); }
+template <>
+__device__ inline void epi<3, float>(long long r, float k, float *v, double *v64, float *yn, float *acc,
+                                     const HConst &hc) { epi32<3>(r, k, v, v64, yn, acc, hc); }
+template <>
+__device__ inline void epi<4, float>(long long r, float k, float *v, double *v64, float *yn, float *acc,
+                                     const HConst &hc) { epi32<4>(r, k, v, v64, yn, acc, hc); }
+
+template <int STAGE, typename VT>
+__device__ inline bool long_rows_part(const HybView<VT> &A0, const HybView<VT> &A1, const StepArgs &a, VT eps,
+                                      const VT *__restrict__ y, VT *v, double *v64, VT *yn, VT *acc) {
+    if ((int)blockIdx.x >= a.nb_long) return false;
+    int lane = threadIdx.x & 31;
+    long long i = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (i < a.n_long) {
+        VT s0 = tail_dot<VT, VT>(A0, i, lane, y);
+        VT s1 = tail_dot<VT, VT>(A1, i, lane, y);
+        if (lane == 0) epi<STAGE, VT>(a.long_rows[i], s0 + eps * s1, v, v64, yn, acc, a.hc);
+    }
+    return true;
+}
+
+// Variant 1: the whole ELL row is loaded into registers (all columns, then all values, then
+// all gathers) before the products, with a larger register budget for the loads in flight.
+template <int STAGE, int W, typename VT>
+__global__ void __launch_bounds__(kThreads, 3) k_stage_pf(HybView<VT> A0, HybView<VT> A1, StepArgs a,
+                                                          const VT *__restrict__ y, VT *v, double *v64,
+                                                          VT *__restrict__ yn, VT *__restrict__ acc) {
+    __shared__ VT s_eps;
+    if (threadIdx.x == 0) s_eps = (VT)a.eps_tab[3 * (*a.base + a.local) + eps_slot<STAGE>()];
+    __syncthreads();
+    const VT eps = s_eps;
+    if (long_rows_part<STAGE, VT>(A0, A1, a, eps, y, v, v64, yn, acc)) return;
+    long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
+    if (r >= a.D) return;
+    int c[W];
+    VT x[W], m[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) c[j] = ldcs(A0.ell_col + (long long)j * A0.ld + r);
+    if (c[0] < 0) return;
+#pragma unroll
+    for (int j = 0; j < W; ++j) m[j] = ldcs(A0.ell_val + (long long)j * A0.ld + r);
+#pragma unroll
+    for (int j = 0; j < W; ++j) x[j] = __ldg(y + c[j]);
+    VT s0 = m[0] * x[0];
+#pragma unroll
+    for (int j = 1; j < W; ++j) s0 += m[j] * x[j];
+    VT s1 = ell_dot_full<VT, VT>(A1, r, y);
+    epi<STAGE, VT>(r, s0 + eps * s1, v, v64, yn, acc, a.hc);
+}
+
+// Variant 2: two consecutive rows per thread with 2-wide vector loads of the slot-major ELL
+// arrays (ld is a multiple of 32 and r is even, so every vector access is aligned).
+template <int STAGE, int W, typename VT>
+__global__ void __launch_bounds__(kThreads) k_stage_r2(HybView<VT> A0, HybView<VT> A1, StepArgs a,
+                                                       const VT *__restrict__ y, VT *v, double *v64,
+                                                       VT *__restrict__ yn, VT *__restrict__ acc) {
+    using V2 = typename Vec2<VT>::T;
+    __shared__ VT s_eps;
+    if (threadIdx.x == 0) s_eps = (VT)a.eps_tab[3 * (*a.base + a.local) + eps_slot<STAGE>()];
+    __syncthreads();
+    const VT eps = s_eps;
+    if (long_rows_part<STAGE, VT>(A0, A1, a, eps, y, v, v64, yn, acc)) return;
+    long long r = ((long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x) * 2;
+    if (r >= a.D) return;
+    const int w0 = W > 0 ? W : A0.width;
+    int2 c = ldcs((const int2 *)(A0.ell_col + r));
+    V2 m = ldcs((const V2 *)(A0.ell_val + r));
+    const bool live0 = c.x >= 0, live1 = (r + 1 < a.D) && c.y >= 0;
+    VT sa = m.x * __ldg(y + (c.x < 0 ? 0 : c.x));
+    VT sb = m.y * __ldg(y + (c.y < 0 ? 0 : c.y));
+#pragma unroll
+    for (int j = 1; j < (W > 0 ? W : 64); ++j) {
+        if (W == 0 && j >= w0) break;
+        long long p = (long long)j * A0.ld + r;
+        int2 cj = ldcs((const int2 *)(A0.ell_col + p));
+        V2 mj = ldcs((const V2 *)(A0.ell_val + p));
+        sa += mj.x * __ldg(y + cj.x);
+        sb += mj.y * __ldg(y + cj.y);
+    }
+    VT ta = VT(0), tb = VT(0);
+    for (int j = 0; j < A1.width; ++j) {
+        long long p = (long long)j * A1.ld + r;
+        int2 cj = ldcs((const int2 *)(A1.ell_col + p));
+        V2 mj = ldcs((const V2 *)(A1.ell_val + p));
+        ta += mj.x * __ldg(y + cj.x);
+        tb += mj.y * __ldg(y + cj.y);
+    }
+    if (live0) epi<STAGE, VT>(r, sa + eps * ta, v, v64, yn, acc, a.hc);
+    if (live1) epi<STAGE, VT>(r + 1, sb + eps * tb, v, v64, yn, acc, a.hc);
+}
+
 __global__ void k_to_f32(const double *__restrict__ v, float *__restrict__ o, long long n) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) o[i] = (float)v[i];
@@ -244,23 +365,102 @@ void step32_w(gksl_ctx *c, const Launch &L) {
     k_stage32<4, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yA32.p, c->v32.p, c->v.p, nullptr, c->acc32.p);
 }
 
+// variants 1 and 2 on either precision
+template <int VAR, int W, typename VT>
+void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h1, VT *v, double *v64, VT *ya, VT *yb,
+              VT *acc) {
+    auto A0 = view(h0), A1 = view(h1);
+    cudaStream_t s = c->stream;
+    Launch L = L0;
+    if (VAR == 2) L.grid = (unsigned)(L.a.nb_long + (c->D + 2 * kThreads - 1) / (2 * kThreads));
+    if constexpr (VAR == 1) {
+        k_stage_pf<1, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, ya, acc);
+        k_stage_pf<2, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, ya, v, v64, yb, acc);
+        k_stage_pf<3, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, yb, v, v64, ya, acc);
+        k_stage_pf<4, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, ya, v, v64, nullptr, acc);
+    } else {
+        k_stage_r2<1, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, ya, acc);
+        k_stage_r2<2, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, ya, v, v64, yb, acc);
+        k_stage_r2<3, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, yb, v, v64, ya, acc);
+        k_stage_r2<4, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, ya, v, v64, nullptr, acc);
+    }
+}
+
 void launch_step(gksl_ctx *c, int precision, double h, const double *tab, long long local) {
     Launch L = make_launch(c, c->hyb0, h, tab, local);
     int W = c->hyb0.width;
+    int var = c->rk4_var[precision == 64 ? 0 : 1];
+    if (var == 1 && W != 18) var = 0;   // the register-prefetch variant exists for the 18-slot layout only
     if (precision == 64) {
-        if (W == 18) step64_w<18>(c, L);
+        if (var == 1) step_var<1, 18, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, c->yA.p, c->yB.p, c->acc.p);
+        else if (var == 2 && W == 18)
+            step_var<2, 18, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, c->yA.p, c->yB.p, c->acc.p);
+        else if (var == 2) step_var<2, 0, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, c->yA.p, c->yB.p, c->acc.p);
+        else if (W == 18) step64_w<18>(c, L);
         else step64_w<0>(c, L);
     } else {
-        if (W == 18) step32_w<18>(c, L);
+        if (var == 1) step_var<1, 18, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, c->yA32.p, c->yB32.p, c->acc32.p);
+        else if (var == 2 && W == 18)
+            step_var<2, 18, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, c->yA32.p, c->yB32.p, c->acc32.p);
+        else if (var == 2)
+            step_var<2, 0, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, c->yA32.p, c->yB32.p, c->acc32.p);
+        else if (W == 18) step32_w<18>(c, L);
         else step32_w<0>(c, L);
     }
     GK_LAUNCH_CHECK();
 }
 
+// Time the stage-kernel variants on this context's matrix (a few steps each, from a saved
+// copy of the state, which is restored afterwards) and keep the fastest.  Small systems are
+// launch-latency bound and keep variant 0.  GKSL_RK4_VARIANT=0|1|2 forces a variant.
+void tune_variant(gksl_ctx *c, int precision, double h, const double *tab) {
+    int pi = precision == 64 ? 0 : 1;
+    if (c->rk4_tuned[pi]) return;
+    c->rk4_tuned[pi] = true;
+    const char *env = getenv("GKSL_RK4_VARIANT");
+    if (env && env[0] >= '0' && env[0] <= '2') {
+        c->rk4_var[pi] = env[0] - '0';
+        return;
+    }
+    c->rk4_var[pi] = 0;
+    if (c->D < 65536) return;
+    long long D1 = c->D + 1;
+    DBuf<double> save((size_t)D1);
+    GK_CUDA(cudaMemcpyAsync(save.p, c->v.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, c->stream));
+    cudaEvent_t e0, e1;
+    GK_CUDA(cudaEventCreate(&e0));
+    GK_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_v = 0;
+    for (int var = 0; var < 3; ++var) {
+        c->rk4_var[pi] = var;
+        k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, 0);
+        for (int i = 0; i < 2; ++i) launch_step(c, precision, h, tab, i);
+        GK_CUDA(cudaEventRecord(e0, c->stream));
+        for (int i = 2; i < 8; ++i) launch_step(c, precision, h, tab, i);
+        GK_CUDA(cudaEventRecord(e1, c->stream));
+        GK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        c->rk4_var_us[pi][var] = 1000.0 * ms / 6.0;
+        if (ms < best) { best = ms; best_v = var; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->rk4_var[pi] = best_v;
+    GK_CUDA(cudaMemcpyAsync(c->v.p, save.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, c->stream));
+    if (precision == 32) {
+        k_to_f32<<<grid_for(D1, 256), 256, 0, c->stream>>>(c->v.p, c->v32.p, D1);
+        GK_LAUNCH_CHECK();
+    }
+    GK_CUDA(cudaStreamSynchronize(c->stream));
+}
+
 // one CUDA graph per (chunk length, precision, h); replayed with the step base set before
 cudaGraphExec_t graph_for(gksl_ctx *c, long long steps, int precision, double h, const double *tab) {
+    const int var = c->rk4_var[precision == 64 ? 0 : 1];
     for (auto &g : c->graphs)
-        if (g.steps == steps && g.precision == precision && g.h == h) return g.exec;
+        if (g.steps == steps && g.precision == precision && g.h == h && g.variant == var) return g.exec;
     cudaGraph_t graph;
     GK_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     for (long long i = 0; i < steps; ++i) launch_step(c, precision, h, tab, i);
@@ -268,7 +468,7 @@ cudaGraphExec_t graph_for(gksl_ctx *c, long long steps, int precision, double h,
     cudaGraphExec_t exec;
     GK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
     GK_CUDA(cudaGraphDestroy(graph));
-    c->graphs.push_back({steps, precision, h, exec});
+    c->graphs.push_back({steps, precision, h, exec, var});
     return exec;
 }
 
@@ -386,12 +586,13 @@ void propagate(gksl_ctx *c, long long spp, long long n_steps, int precision, lon
     ensure_work(c, precision == 32);
     const double T = 2.0 * M_PI / c->omega;
     const double h = T / (double)spp;
-    fill_eps_table(c, c->t, h, n_steps);
+    fill_eps_table(c, c->t, h, std::max(n_steps, 8LL));   // the variant timing below uses 8 steps
     DBuf<double> &tab = c->eps_tab;
     if (precision == 32) {
         k_to_f32<<<grid_for(c->D + 1, 256), 256, 0, c->stream>>>(c->v.p, c->v32.p, c->D + 1);
         GK_LAUNCH_CHECK();
     }
+    if (n_steps > 0) tune_variant(c, precision, h, tab.p);
     long long n = 0, emitted = 0;
     while (n < n_steps) {
         long long stop = n_steps;

@@ -160,6 +160,31 @@ def test_min_stable_steps_and_divergence_guard(G):
         G.gksl_destroy(ctx)
 
 
+@pytest.mark.parametrize("variant", ["0", "1", "2"])
+def test_stage_kernel_variants(G, variant, monkeypatch):
+    """Every stage-kernel variant (forced; normally chosen by timing) on a system large enough
+    to be tuned (N = 300, D = 89 999), FP64 against the oracle and FP32 within its tolerance."""
+    monkeypatch.setenv("GKSL_RK4_VARIANT", variant)
+    d = W.dimer(300)
+    ctx = G.dimer_context(d, flags=G.GKSL_ASM_FP32)
+    try:
+        spp = G.gksl_min_stable_steps(ctx)
+        D = d.N * d.N - 1
+        nst = 70   # one 64-step graph chunk plus a remainder
+        out = run_gpu(G, ctx, spp, nst, nst, D=D)
+        info = G.gksl_get_info(ctx)
+        assert info.rk4_variant[0] == int(variant)
+        u = SYS.unfold_dimer(d)
+        v_ref, _ = SYS.propagate_dimer(d, u, spp, nst)
+        assert np.abs(out[0] - v_ref).max() < TOL64
+        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+        o32 = run_gpu(G, ctx, spp, nst, nst, precision=32, D=D)
+        assert G.gksl_get_info(ctx).rk4_variant[1] == int(variant)
+        assert np.abs(o32[0] - v_ref).max() < TOL32_V
+    finally:
+        G.gksl_destroy(ctx)
+
+
 def test_config4_n1000_fp64_steps(G):
     """Largest workload (N = 1000, D = 999999) in the launch configuration of the benchmark:
     a few FP64 steps at the stable step size against the oracle's RK4 on its own matrices."""
