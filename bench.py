@@ -28,7 +28,9 @@ N_BENCH = 1000
 STEP_RK4 = 2000          # RK4 steps per bench step
 METRIC = "RK4 steps/s & SpMV HBM GB/s at N=1000; Q/K assembly s; batched/adjoint vs plain"
 UNIT = "RK4 steps/s"
-PROFILE_JSON = os.path.join(ROOT, "profiles", "rk4_stage64_n1000.json")
+PROFILE_JSON = os.path.join(ROOT, "profiles", "rk4_stage_fp64_n1000.json")
+# stage-kernel variants of the library (chosen per context by timing)
+KERNEL_OF_VARIANT = {0: "k_stage64<S,18>", 1: "k_stage_pf<S,18,double>", 2: "k_stage_r2<S,18,double>"}
 
 
 def dist_env():
@@ -204,6 +206,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case for ncu: N=1000 assembly, then 50 FP64 and 50 FP32 RK4 steps")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="profiling case for ncu: the 256-instance batch, 40 steps per group")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -211,6 +215,9 @@ def main():
         return
     if args.profile:
         run_profile_case()
+        return
+    if args.profile_batch:
+        run_profile_batch()
         return
 
     import torch
@@ -266,14 +273,16 @@ def main():
     bytes_launch = stage_bytes(info.nnz_q0, info.nnz_q1, D, 64)
     hbm, peak_kind = peaks()
     achieved = bytes_launch / (avg_launch_ms * 1e-3) / 1e9
+    variant = G.gksl_get_info(ctx).rk4_variant[0]
+    kernel = KERNEL_OF_VARIANT.get(variant, "?")
     traffic = None
     if os.path.exists(PROFILE_JSON):
         pj = json.load(open(PROFILE_JSON))
-        if pj.get("src_hash") == src_hash():
+        if pj.get("src_hash") == src_hash() and pj.get("variant") == variant:
             traffic = pj.get("dram_bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch,
-                "kernel": "k_stage64<*,18> (fused SpMV + RK4 stage update)"}
+                "kernel": kernel + " (fused SpMV + RK4 stage update, FP64)"}
 
     # end to end through the C ABI with pinned host buffers: H2D of v, propagate, D2H of v
     host_in = torch.empty(D, dtype=torch.float64, pin_memory=True)
@@ -353,31 +362,32 @@ def run_profile_case():
     G.gksl_destroy(ctx)
 
 
+def run_profile_batch():
+    """Small, fixed case for ncu: the 256-instance seeded batch (N in {50, 100, 200}), 40 FP32 steps
+    per group after the tile autotuning."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1812_11626_gb300 import gksl as G
+    from paper_1812_11626_gb300 import workloads as W
+    b, ctxs, groups = G.dimer_batch(W.batch_instances(256, 1812))
+    spps = [spp for _, _, spp in groups]
+    sec = G.gksl_batch_propagate(b, spps, [40] * len(groups), 0)
+    print(json.dumps({"profile_case": "batch 256", "seconds": sec,
+                      "tiles": [G.gksl_batch_info(b, i) for i in range(len(groups))]}), flush=True)
+    G.gksl_batch_destroy(b)
+    for c in ctxs:
+        G.gksl_destroy(c)
+
+
 def batched_and_adjoint(G, W, torch):
     """Side measurements: the batched form (256 seeded instances, N in {50, 100, 200}) and the
     adjoint gradient at N = 200, each against the plain FP64 single-instance path."""
     out = {}
     inst = W.batch_instances(256, 1812)
-    groups = {}
-    for i in inst:
-        groups.setdefault(i["N"], []).append(i)
-    ctxs, n_inst, A, g, spps = [], [], [], [], []
-    for N in sorted(groups):
-        d = W.dimer(N)
-        d.rate = 1.0 / (N - 1)
-        c = G.dimer_context(d, flags=G.GKSL_ASM_FP32)
-        ctxs.append(c)
-        n_inst.append(len(groups[N]))
-        A += [x["A"] for x in groups[N]]
-        g += [x["gamma"] for x in groups[N]]
-        # stable step count for the largest A and gamma of the group
-        G.gksl_set_drive(c, d.params["E"], max(x["A"] for x in groups[N]), d.params["omega"])
-        G.gksl_set_gamma(c, 0, max(x["gamma"] for x in groups[N]) / (N - 1))
-        spps.append(G.gksl_min_stable_steps(c))
-        G.gksl_set_gamma(c, 0, 1.0 / (N - 1))
-        G.gksl_set_drive(c, d.params["E"], d.params["A"], d.params["omega"])
-        G.gksl_assemble(c, G.GKSL_ASM_FP32)
-    b = G.gksl_batch_create(ctxs, n_inst, A, g)
+    b, ctxs, groups = G.dimer_batch(inst)
+    spps = [spp for _, _, spp in groups]
+    n_inst = [len(idx) for _, idx, _ in groups]
+    groups = {N: idx for N, idx, _ in groups}
     # a tenth of a period per group at its stable step size (the per-step cost is what is timed)
     steps = [max(1, s // 10) for s in spps]
     G.gksl_batch_propagate(b, spps, steps, 0)   # warm-up, includes the tile autotuning

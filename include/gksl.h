@@ -88,6 +88,14 @@ gksl_status gksl_set_gamma(gksl_ctx *ctx, int p, double gamma_p);
 /* eps(t) = E + A sin(omega t), omega > 0; the period is T = 2 pi / omega (Sec. III). */
 gksl_status gksl_set_drive(gksl_ctx *ctx, double E, double A, double omega);
 
+#define GKSL_DRIVE_SIN 0     /* theta(t) = sin(omega t) (default) */
+#define GKSL_DRIVE_SQUARE 1  /* theta(t) = +1 on [0, T/2), -1 on [T/2, T), periodic (Sec. III, driving (i)) */
+/* Shape of theta in eps(t) = E + A theta(t).  With the square shape every RK4 step uses theta at
+ * its midpoint for all four stages (the drive is constant on each step of a grid that contains
+ * the jumps), so propagation requires an even steps_per_period and a start time on the step grid
+ * (GKSL_ERR_ARG otherwise).  Batches take the shape of their group contexts. */
+gksl_status gksl_set_drive_shape(gksl_ctx *ctx, int shape);
+
 /* ------------------------------------------------------------------ expansion (Sec. IV step 2.1) */
 
 /* Coefficients x_s = Tr(F_s X), s < D, of an N x N CSR matrix X (host or device arrays).
@@ -191,6 +199,11 @@ void gksl_batch_destroy(gksl_batch *b);
 /* Message of the last failed call on this batch; with b == NULL, of the calling thread's last
  * failed gksl_batch_create. */
 const char *gksl_batch_last_error(const gksl_batch *b);
+/* Give every instance its own weight theta_b of Hamiltonian component `component` (a parameter
+ * scan, e.g. the interaction U of a bifurcation diagram): instance b then uses theta_b in place of
+ * its group context's theta_k.  theta_b holds one value per instance in the batch's order (host or
+ * device).  Adds a fourth value channel Q(H0_k) to every group; the tile autotuning is redone. */
+gksl_status gksl_batch_set_scan(gksl_batch *b, int component, const double *theta_b);
 /* Reset every instance to its group's current state vector, t = 0. */
 gksl_status gksl_batch_reset(gksl_batch *b);
 /* Advance group i by n_steps[i] RK4 steps of h = T / steps_per_period[i] from the batch's current

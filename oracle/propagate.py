@@ -27,25 +27,45 @@ def eps_fn(E, A, omega):
     return lambda t: E + A * np.sin(omega * t)
 
 
-def rk4(Q0, Q1, K, eps, v0, h, nsteps, t0=0.0, emit_every=None, emit_fn=None):
+def square_theta(t, omega):
+    """Sec. III driving (i): theta = +1 on [0, T/2), -1 on [T/2, T), periodic, T = 2 pi / omega."""
+    T = 2 * np.pi / omega
+    return 1.0 if (t % T) < 0.5 * T else -1.0
+
+
+def eps_square_step(E, A, omega):
+    """Stage values of eps for the square drive (reading): the drive is constant on every step of a
+    grid that contains its jumps, so all stages of the step use theta at the step's midpoint."""
+    def stages(t, h):
+        e = E + A * square_theta(t + 0.5 * h, omega)
+        return e, e, e
+    return stages
+
+
+def rk4(Q0, Q1, K, eps, v0, h, nsteps, t0=0.0, emit_every=None, emit_fn=None, eps_step=None):
     """Classical RK4 on dv/dt = (Q0 + eps(t) Q1) v + K.
 
     Q0, Q1 are anything with ``@`` (scipy sparse or dense). Returns the final v and
     the list of emitted values (v, or emit_fn(v), every ``emit_every`` steps).
-    Works in complex arithmetic too (complex-step derivatives).
+    ``eps_step(t_n, h)``, when given, supplies the three stage values (t_n, t_n + h/2, t_n + h)
+    instead of eps(t) at the stage times.  Works in complex arithmetic too (complex-step).
     """
     v = np.array(v0, copy=True)
     out = []
 
-    def f(t, y):
-        return Q0 @ y + eps(t) * (Q1 @ y) + K
+    def f(e, y):
+        return Q0 @ y + e * (Q1 @ y) + K
 
     for n in range(nsteps):
         t = t0 + n * h
-        k1 = f(t, v)
-        k2 = f(t + 0.5 * h, v + 0.5 * h * k1)
-        k3 = f(t + 0.5 * h, v + 0.5 * h * k2)
-        k4 = f(t + h, v + h * k3)
+        if eps_step is not None:
+            e1, e2, e4 = eps_step(t, h)
+        else:
+            e1, e2, e4 = eps(t), eps(t + 0.5 * h), eps(t + h)
+        k1 = f(e1, v)
+        k2 = f(e2, v + 0.5 * h * k1)
+        k3 = f(e2, v + 0.5 * h * k2)
+        k4 = f(e4, v + h * k3)
         v = v + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
         if emit_every and (n + 1) % emit_every == 0:
             out.append(emit_fn(v) if emit_fn else v.copy())

@@ -47,8 +47,10 @@ def initial_v(d):
     return _b.expand_sparse(rho0).real
 
 
-def propagate_dimer(d, u, steps_per_period, nsteps, emit_every=None, v0=None, t0=0.0):
-    """RK4 of the dimer from v0 (default v(0)); returns (v_final, emitted list)."""
+def propagate_dimer(d, u, steps_per_period, nsteps, emit_every=None, v0=None, t0=0.0, drive="sin"):
+    """RK4 of the dimer from v0 (default v(0)); returns (v_final, emitted list).
+
+    drive: "sin" (theta = sin(omega t)) or "square" (theta = +-1, Sec. III driving (i))."""
     p = d.params
     T = 2 * np.pi / p["omega"]
     h = T / steps_per_period
@@ -56,5 +58,6 @@ def propagate_dimer(d, u, steps_per_period, nsteps, emit_every=None, v0=None, t0
     K = d.rate * u.K1
     if v0 is None:
         v0 = initial_v(d)
+    step = _p.eps_square_step(p["E"], p["A"], p["omega"]) if drive == "square" else None
     return _p.rk4(Q0, u.Q1, K, _p.eps_fn(p["E"], p["A"], p["omega"]), v0, h, nsteps, t0=t0,
-                  emit_every=emit_every)
+                  emit_every=emit_every, eps_step=step)

@@ -177,6 +177,7 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
     const double h = T / (double)S;
     const long long nsteps = period * S, first = (period - 1) * S;
     const double t0 = c->t;
+    check_drive_grid(c, S, h);
     fill_eps_table(c, t0, h, nsteps);
 
     // channel descriptors
@@ -298,7 +299,9 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
             for (long long i = len - 1; i >= 0; --i) {
                 const long long gstep = p * S + j * q + i;
                 const double tn = t0 + (double)gstep * h;
-                const double ts[4] = {tn, tn + 0.5 * h, tn + 0.5 * h, tn + h};
+                double th3[3];
+                drive_theta(c->drive_shape, c->omega, tn, h, th3);
+                const double thst[4] = {th3[0], th3[1], th3[1], th3[2]};   // theta at stages 1..4
                 const long long m = gstep - first;
                 const double beta = (m >= 0 && m < S) ? wt[m] : 0.0;
                 double *vn = traj.p + i * D1;
@@ -306,7 +309,7 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
                     forward_stage_inputs(c, 64, h, gstep, vn, Y2d.p, Y3d.p, Y4d.p);
                     const double *Ys[4] = {vn, Y2d.p, Y3d.p, Y4d.p};
                     for (int st = 4; st >= 1; --st) {
-                        double sn = std::sin(c->omega * ts[st - 1]);
+                        double sn = thst[st - 1];
                         if (q1ch >= 0) {
                             a64.chw[q1ch] = c->E + c->A * sn;
                             a64.gfac[q1ch] = sn;
@@ -330,7 +333,7 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
                     to_f32(lam.p, lamf.p, D1, s);
                     const float *Ys[4] = {Y1f.p, Y2f.p, Y3f.p, Y4f.p};
                     for (int st = 4; st >= 1; --st) {
-                        double sn = std::sin(c->omega * ts[st - 1]);
+                        double sn = thst[st - 1];
                         if (q1ch >= 0) {
                             a32.chw[q1ch] = c->E + c->A * sn;
                             a32.gfac[q1ch] = sn;

@@ -293,6 +293,14 @@ extern "C" gksl_status gksl_set_drive(gksl_ctx *c, double E, double A, double om
     });
 }
 
+extern "C" gksl_status gksl_set_drive_shape(gksl_ctx *c, int shape) {
+    return guarded(c, [&] {
+        GK_REQUIRE(shape == GKSL_DRIVE_SIN || shape == GKSL_DRIVE_SQUARE, GKSL_ERR_ARG, "unknown drive shape");
+        c->drive_shape = shape;
+        clear_graphs(c);
+    });
+}
+
 // ====================================================================== expansion
 
 extern "C" gksl_status gksl_expand(gksl_ctx *c, const int *rowptr, const int *col, const double *re, const double *im,

@@ -31,13 +31,20 @@ constexpr int kMaxIpl = 4;
 constexpr int kMaxGroups = 8;
 constexpr int kBatchGraphSteps = 32;
 
+constexpr int kMaxCh = 4;   // QH, Q1, [R | K], and optionally one scanned Hamiltonian component
+
 struct GroupDev {
-    const int *ptr[3];
-    const int *col[3];
-    const float *vf[3];
-    const double *vd[3];
+    const int *ptr[kMaxCh];
+    const int *col[kMaxCh];
+    const float *vf[kMaxCh];
+    const double *vd[kMaxCh];
+    int nch;                  // 3, or 4 with a scanned component
+    const double *S;          // per-instance coefficient of channel 3 (theta_b - theta_k)
+    const float *Sf;
     long long D;
     int B, ipl, nchunks;
+    long long Bs;   // row stride of the state matrices: B rounded up to 4 (16-byte rows)
+    int vec4;       // FP32 steps use the 4-instances-per-lane path
     long long nsteps;
     double h, h2, h6;   // h, h/2, h/6 (computed on the host)
     float hf, h2f, h6f;
@@ -59,6 +66,162 @@ struct BatchArgs {
     long long local;
 };
 
+// Stage update of element o = r * Bs + b (instance b of row r) from k.
+template <int STAGE, bool F64>
+__device__ inline void stage_update(const GroupDev &G, long long o, double kd, float kf) {
+    if (F64) {
+        double *yn = STAGE == 1 ? G.Y64[0] : (STAGE == 2 ? G.Y64[1] : G.Y64[0]);
+        if (STAGE == 1) { yn[o] = G.V64[o] + G.h2 * kd; G.ACC64[o] = kd; }
+        if (STAGE == 2) { yn[o] = G.V64[o] + G.h2 * kd; G.ACC64[o] += 2.0 * kd; }
+        if (STAGE == 3) { yn[o] = G.V64[o] + G.h * kd; G.ACC64[o] += 2.0 * kd; }
+        if (STAGE == 4) { G.V64[o] = G.V64[o] + G.h6 * (G.ACC64[o] + kd); G.V32[o] = (float)G.V64[o]; }
+    } else {
+        float *yn = STAGE == 1 ? G.Y32[0] : (STAGE == 2 ? G.Y32[1] : G.Y32[0]);
+        if (STAGE == 1) { yn[o] = G.V32[o] + G.h2f * kf; G.ACC32[o] = kf; }
+        if (STAGE == 2) { yn[o] = G.V32[o] + G.h2f * kf; G.ACC32[o] += 2.0f * kf; }
+        if (STAGE == 3) { yn[o] = G.V32[o] + G.hf * kf; G.ACC32[o] += 2.0f * kf; }
+        if (STAGE == 4) {
+            float inc = G.h6f * (G.ACC32[o] + kf);
+            double nv = G.V64[o] + (double)inc;
+            G.V64[o] = nv;
+            G.V32[o] = (float)nv;
+        }
+    }
+}
+
+// Row r for the instances b0 + 32 k, k < ipl, of this lane (scalar gathers).
+template <int STAGE, bool F64>
+__device__ inline void row_scalar(const GroupDev &G, long long r, int ch, int lane, long long step) {
+    using VT = typename std::conditional<F64, double, float>::type;
+    const int B = G.B;
+    const long long Bs = G.Bs;
+    const VT *X;
+    if (F64) X = (const VT *)(STAGE == 1 ? (void *)G.V64 : (STAGE == 3 ? (void *)G.Y64[1] : (void *)G.Y64[0]));
+    else X = (const VT *)(STAGE == 1 ? (void *)G.V32 : (STAGE == 3 ? (void *)G.Y32[1] : (void *)G.Y32[0]));
+    VT acc[kMaxCh][kMaxIpl];
+#pragma unroll
+    for (int c = 0; c < kMaxCh; ++c)
+#pragma unroll
+        for (int k = 0; k < kMaxIpl; ++k) acc[c][k] = VT(0);
+    const int b0 = ch * 32 * G.ipl + lane;
+    // entries in groups of 4: load their columns and values, then issue every gather of the
+    // group before the products, so each warp keeps several loads in flight
+    constexpr int U = 4;
+#pragma unroll
+    for (int c = 0; c < kMaxCh; ++c) {
+        if (c >= G.nch) break;
+        const int e1 = G.ptr[c][r + 1];
+        int e = G.ptr[c][r];
+        for (; e + U <= e1; e += U) {
+            int col[U];
+            VT v[U], x[U][kMaxIpl];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                col[u] = G.col[c][e + u];
+                v[u] = F64 ? (VT)G.vd[c][e + u] : (VT)G.vf[c][e + u];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int k = 0; k < kMaxIpl; ++k) {
+                    int b = b0 + 32 * k;
+                    x[u][k] = (k < G.ipl && b < B) ? __ldg(X + (long long)col[u] * Bs + b) : VT(0);
+                }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int k = 0; k < kMaxIpl; ++k) acc[c][k] += v[u] * x[u][k];
+        }
+        for (; e < e1; ++e) {
+            const int col = G.col[c][e];
+            const VT v = F64 ? (VT)G.vd[c][e] : (VT)G.vf[c][e];
+            const VT *xr = X + (long long)col * Bs;
+#pragma unroll
+            for (int k = 0; k < kMaxIpl; ++k) {
+                int b = b0 + 32 * k;
+                if (k < G.ipl && b < B) acc[c][k] += v * __ldg(xr + b);
+            }
+        }
+    }
+    const int slot = STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1);
+    const long long ts = 3 * step + slot;
+#pragma unroll
+    for (int k = 0; k < kMaxIpl; ++k) {
+        int b = b0 + 32 * k;
+        if (k >= G.ipl || b >= B) continue;
+        long long o = r * Bs + b;
+        if (F64) {
+            double kd = acc[0][k] + (G.A[b] * G.sin_tab[ts]) * acc[1][k] + G.g[b] * acc[2][k];
+            if (G.nch > 3) kd += G.S[b] * acc[3][k];
+            stage_update<STAGE, true>(G, o, kd, 0.0f);
+        } else {
+            float kf = (float)(acc[0][k] + (G.Af[b] * G.sin_tab_f[ts]) * acc[1][k] + G.gf[b] * acc[2][k]);
+            if (G.nch > 3) kf += G.Sf[b] * (float)acc[3][k];
+            stage_update<STAGE, false>(G, o, 0.0, kf);
+        }
+    }
+}
+
+// Row r for 4 consecutive instances per lane (128 per warp), one 16-byte gather per entry.
+template <int STAGE>
+__device__ inline void row_vec4(const GroupDev &G, long long r, int ch, int lane, long long step) {
+    const int bq = ch * 128 + 4 * lane;
+    if (bq >= G.B) return;
+    const long long Bs = G.Bs;
+    const float *X = STAGE == 1 ? G.V32 : (STAGE == 3 ? G.Y32[1] : G.Y32[0]);
+    float4 acc[kMaxCh];
+#pragma unroll
+    for (int c = 0; c < kMaxCh; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    constexpr int U = 4;
+#pragma unroll
+    for (int c = 0; c < kMaxCh; ++c) {
+        if (c >= G.nch) break;
+        const int e1 = G.ptr[c][r + 1];
+        int e = G.ptr[c][r];
+        for (; e + U <= e1; e += U) {
+            int col[U];
+            float v[U];
+            float4 x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                col[u] = G.col[c][e + u];
+                v[u] = G.vf[c][e + u];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) x[u] = __ldg((const float4 *)(X + (long long)col[u] * Bs + bq));
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                acc[c].x += v[u] * x[u].x;
+                acc[c].y += v[u] * x[u].y;
+                acc[c].z += v[u] * x[u].z;
+                acc[c].w += v[u] * x[u].w;
+            }
+        }
+        for (; e < e1; ++e) {
+            const float v = G.vf[c][e];
+            const float4 x = __ldg((const float4 *)(X + (long long)G.col[c][e] * Bs + bq));
+            acc[c].x += v * x.x;
+            acc[c].y += v * x.y;
+            acc[c].z += v * x.z;
+            acc[c].w += v * x.w;
+        }
+    }
+    const int slot = STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1);
+    const float sn = G.sin_tab_f[3 * step + slot];
+    const float a0[4] = {acc[0].x, acc[0].y, acc[0].z, acc[0].w};
+    const float a1[4] = {acc[1].x, acc[1].y, acc[1].z, acc[1].w};
+    const float a2[4] = {acc[2].x, acc[2].y, acc[2].z, acc[2].w};
+    const float a3[4] = {acc[3].x, acc[3].y, acc[3].z, acc[3].w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int b = bq + k;
+        if (b >= G.B) break;
+        float kf = a0[k] + (G.Af[b] * sn) * a1[k] + G.gf[b] * a2[k];
+        if (G.nch > 3) kf += G.Sf[b] * a3[k];
+        stage_update<STAGE, false>(G, r * Bs + b, 0.0, kf);
+    }
+}
+
 template <int STAGE, bool F64>
 __global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
     const long long step = *a.base + a.local;
@@ -72,96 +235,19 @@ __global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
         long long r = (tl / G.nchunks) * kRowsPerTile + warp;
         int ch = (int)(tl % G.nchunks);
         if (r >= G.D) continue;
-        const int B = G.B;
-        using VT = typename std::conditional<F64, double, float>::type;
-        const VT *X;
-        if (F64) X = (const VT *)(STAGE == 1 ? G.V64 : (STAGE == 3 ? G.Y64[1] : G.Y64[0]));
-        else X = (const VT *)(STAGE == 1 ? (void *)G.V32 : (STAGE == 3 ? (void *)G.Y32[1] : (void *)G.Y32[0]));
-        VT acc[3][kMaxIpl];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int k = 0; k < kMaxIpl; ++k) acc[c][k] = VT(0);
-        const int b0 = ch * 32 * G.ipl + lane;
-        // entries in groups of 4: load their columns and values, then issue every gather of the
-        // group before the products, so each warp keeps several loads in flight
-        constexpr int U = 4;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int e1 = G.ptr[c][r + 1];
-            int e = G.ptr[c][r];
-            for (; e + U <= e1; e += U) {
-                int col[U];
-                VT v[U], x[U][kMaxIpl];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    col[u] = G.col[c][e + u];
-                    v[u] = F64 ? (VT)G.vd[c][e + u] : (VT)G.vf[c][e + u];
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int k = 0; k < kMaxIpl; ++k) {
-                        int b = b0 + 32 * k;
-                        x[u][k] = (k < G.ipl && b < B) ? __ldg(X + (long long)col[u] * B + b) : VT(0);
-                    }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int k = 0; k < kMaxIpl; ++k) acc[c][k] += v[u] * x[u][k];
-            }
-            for (; e < e1; ++e) {
-                const int col = G.col[c][e];
-                const VT v = F64 ? (VT)G.vd[c][e] : (VT)G.vf[c][e];
-                const VT *xr = X + (long long)col * B;
-#pragma unroll
-                for (int k = 0; k < kMaxIpl; ++k) {
-                    int b = b0 + 32 * k;
-                    if (k < G.ipl && b < B) acc[c][k] += v * __ldg(xr + b);
-                }
-            }
-        }
-        const int slot = STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1);
-        const long long ts = 3 * step + slot;
-        const double h = G.h, h2 = G.h2, h6 = G.h6;
-#pragma unroll
-        for (int k = 0; k < kMaxIpl; ++k) {
-            int b = b0 + 32 * k;
-            if (k >= G.ipl || b >= B) continue;
-            long long o = r * B + b;
-            VT kv;
-            if (F64) kv = (VT)(acc[0][k] + (G.A[b] * G.sin_tab[ts]) * acc[1][k] + G.g[b] * acc[2][k]);
-            else kv = (VT)(acc[0][k] + (G.Af[b] * G.sin_tab_f[ts]) * acc[1][k] + G.gf[b] * acc[2][k]);
-            if (F64) {
-                double *yn = STAGE == 1 ? G.Y64[0] : (STAGE == 2 ? G.Y64[1] : G.Y64[0]);
-                double kd = (double)kv;
-                if (STAGE == 1) { yn[o] = G.V64[o] + h2 * kd; G.ACC64[o] = kd; }
-                if (STAGE == 2) { yn[o] = G.V64[o] + h2 * kd; G.ACC64[o] += 2.0 * kd; }
-                if (STAGE == 3) { yn[o] = G.V64[o] + h * kd; G.ACC64[o] += 2.0 * kd; }
-                if (STAGE == 4) { G.V64[o] = G.V64[o] + h6 * (G.ACC64[o] + kd); G.V32[o] = (float)G.V64[o]; }
-            } else {
-                float *yn = STAGE == 1 ? G.Y32[0] : (STAGE == 2 ? G.Y32[1] : G.Y32[0]);
-                float kf = (float)kv, hf = G.hf, h2f = G.h2f, h6f = G.h6f;
-                if (STAGE == 1) { yn[o] = G.V32[o] + h2f * kf; G.ACC32[o] = kf; }
-                if (STAGE == 2) { yn[o] = G.V32[o] + h2f * kf; G.ACC32[o] += 2.0f * kf; }
-                if (STAGE == 3) { yn[o] = G.V32[o] + hf * kf; G.ACC32[o] += 2.0f * kf; }
-                if (STAGE == 4) {
-                    float inc = h6f * (G.ACC32[o] + kf);
-                    double nv = G.V64[o] + (double)inc;
-                    G.V64[o] = nv;
-                    G.V32[o] = (float)nv;
-                }
-            }
-        }
+        if (!F64 && G.vec4) row_vec4<STAGE>(G, r, ch, lane, step);
+        else row_scalar<STAGE, F64>(G, r, ch, lane, step);
     }
 }
 
-__global__ void k_sin_table(double t0, double h, double omega, long long n, double *__restrict__ tab,
+// theta of the drive (sin or square, see drive_theta) at the 3 stage times of each step
+__global__ void k_sin_table(double t0, double h, double omega, int shape, long long n, double *__restrict__ tab,
                             float *__restrict__ tabf) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double tn = t0 + (double)i * h;
-    double s0 = sin(omega * tn), s1 = sin(omega * (tn + 0.5 * h)), s2 = sin(omega * (tn + h));
+    double th[3];
+    drive_theta(shape, omega, t0 + (double)i * h, h, th);
+    double s0 = th[0], s1 = th[1], s2 = th[2];
     tab[3 * i + 0] = s0;
     tab[3 * i + 1] = s1;
     tab[3 * i + 2] = s2;
@@ -208,9 +294,15 @@ struct Group {
     gksl_ctx *ctx = nullptr;
     long long D = 0;
     int B = 0;
-    int ipl = 1;
-    CsrR m[3];            // QH (E folded), Q1, [R | K]
-    DBuf<float> mf[3];    // FP32 values
+    long long Bs = 0;     // B rounded up to 4: the row stride of every state matrix
+    int ipl = 1;          // instances per lane of the scalar FP32 path
+    bool vec4 = true;     // FP32 steps: 4 instances per lane with 16-byte gathers
+    int ipl64 = 1;        // instances per lane of the FP64 steps
+    CsrR m[kMaxCh];       // QH (E folded), Q1, [R | K], scanned component Q(H0_k)
+    DBuf<float> mf[kMaxCh];  // FP32 values
+    int nch = 3;
+    DBuf<double> S;       // per-instance coefficient of the scanned component (theta_b - theta_k)
+    DBuf<float> Sf;
     DBuf<double> A, g, V64, Y64a, Y64b, ACC64, sin_tab;
     DBuf<float> Af, gf, sin_tab_f;
     DBuf<float> V32, Ya, Yb, ACC32;
@@ -251,23 +343,28 @@ __global__ void k_f2(const double *__restrict__ v, float *__restrict__ o, long l
     if (i < n) o[i] = (float)v[i];
 }
 
-BatchArgs make_args(gksl_batch *b, long long local) {
+BatchArgs make_args(gksl_batch *b, bool f64, long long local) {
     BatchArgs a{};
     a.ng = (int)b->groups.size();
     long long tb = 0;
     for (int i = 0; i < a.ng; ++i) {
         Group &G = b->groups[i];
         GroupDev &d = a.gr[i];
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < kMaxCh; ++c) {
             d.ptr[c] = G.m[c].rowptr.p;
             d.col[c] = G.m[c].col.p;
             d.vf[c] = G.mf[c].p;
             d.vd[c] = G.m[c].val.p;
         }
+        d.nch = G.nch;
+        d.S = G.S.p;
+        d.Sf = G.Sf.p;
         d.D = G.D;
         d.B = G.B;
-        d.ipl = G.ipl;
-        d.nchunks = (G.B + 32 * G.ipl - 1) / (32 * G.ipl);
+        d.Bs = G.Bs;
+        d.vec4 = (!f64 && G.vec4) ? 1 : 0;
+        d.ipl = f64 ? G.ipl64 : G.ipl;
+        d.nchunks = d.vec4 ? (G.B + 127) / 128 : (G.B + 32 * d.ipl - 1) / (32 * d.ipl);
         d.nsteps = G.nsteps;
         d.h = G.h;
         d.h2 = 0.5 * G.h;
@@ -309,7 +406,7 @@ unsigned batch_grid(long long ntiles) {
 }
 
 void launch_batch_step(gksl_batch *b, bool f64, long long local) {
-    BatchArgs a = make_args(b, local);
+    BatchArgs a = make_args(b, f64, local);
     unsigned grid = batch_grid(a.ntiles);
     cudaStream_t s = b->stream;
     if (f64) {
@@ -366,10 +463,11 @@ void reset_batch(gksl_batch *b) {
         GK_REQUIRE(c->state_set, GKSL_ERR_STATE, "a group context has no state");
         G.t = 0.0;
         long long rows = G.D + 1;
-        k_replicate<<<grid_for(rows * G.B, 256), 256, 0, b->stream>>>(c->v.p, rows, G.B, G.V64.p, G.V32.p);
+        // every stride slot (padding instances included) gets a finite copy of the state
+        k_replicate<<<grid_for(rows * G.Bs, 256), 256, 0, b->stream>>>(c->v.p, rows, (int)G.Bs, G.V64.p, G.V32.p);
         GK_LAUNCH_CHECK();
-        k_fill_row<<<grid_for(G.B, 128), 128, 0, b->stream>>>(G.V64.p, G.V32.p, G.Ya.p, G.Yb.p, G.Y64a.p, G.Y64b.p,
-                                                               G.D, G.B);
+        k_fill_row<<<grid_for(G.Bs, 128), 128, 0, b->stream>>>(G.V64.p, G.V32.p, G.Ya.p, G.Yb.p, G.Y64a.p, G.Y64b.p,
+                                                                G.D, (int)G.Bs);
         GK_LAUNCH_CHECK();
     }
     GK_CUDA(cudaStreamSynchronize(b->stream));
@@ -392,13 +490,16 @@ void autotune(gksl_batch *b) {
             G->sin_tab.alloc(3 * 64);
             G->sin_tab_f.alloc(3 * 64);
         }
-        k_sin_table<<<1, 64, 0, b->stream>>>(0.0, 1e-6, 1.0, 16, G->sin_tab.p, G->sin_tab_f.p);
+        k_sin_table<<<1, 64, 0, b->stream>>>(0.0, 1e-6, 1.0, 0, 16, G->sin_tab.p, G->sin_tab_f.p);
         GK_LAUNCH_CHECK();
         double best = 1e300;
         int best_ipl = 1;
-        for (int ipl = 1; ipl <= kMaxIpl; ++ipl) {
-            if (32 * (ipl - 1) >= G->B) break;   // wider chunks than the batch add nothing
-            G->ipl = ipl;
+        bool best_vec4 = false;
+        // candidates: the 16-byte gather path (ipl = 0 below), then 1..4 scalar instances per lane
+        for (int ipl = 0; ipl <= kMaxIpl; ++ipl) {
+            if (ipl > 0 && 32 * (ipl - 1) >= G->B) break;   // wider chunks than the batch add nothing
+            G->vec4 = (ipl == 0);
+            G->ipl = ipl == 0 ? 1 : ipl;
             G->h = 1e-6;   // tiny step: the trial leaves the state essentially unchanged
             k_set_base<<<1, 1, 0, b->stream>>>(b->base.p, 0);
             for (int w = 0; w < 2; ++w) launch_batch_step(b, false, w);
@@ -408,9 +509,10 @@ void autotune(gksl_batch *b) {
             GK_CUDA(cudaEventSynchronize(e1));
             float ms = 0;
             GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; best_ipl = ipl; }
+            if (ms < best) { best = ms; best_ipl = G->ipl; best_vec4 = G->vec4; }
         }
         G->ipl = best_ipl;
+        G->vec4 = best_vec4;
         G->tuned_us = best * 1000.0 / 8.0;
         for (size_t i = 0; i < all.size(); ++i) all[i]->nsteps = saved[i];
     }
@@ -554,7 +656,9 @@ extern "C" gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, 
             std::vector<float> fa(hA.begin() + off, hA.begin() + off + G.B), fg(hg.begin() + off, hg.begin() + off + G.B);
             GK_CUDA(cudaMemcpy(G.Af.p, fa.data(), sizeof(float) * G.B, cudaMemcpyHostToDevice));
             GK_CUDA(cudaMemcpy(G.gf.p, fg.data(), sizeof(float) * G.B, cudaMemcpyHostToDevice));
-            long long n = (G.D + 1) * G.B;
+            G.Bs = (G.B + 3) / 4 * 4;
+            G.ipl64 = std::min(kMaxIpl, (G.B + 31) / 32);
+            long long n = (G.D + 1) * G.Bs;
             G.V64.alloc((size_t)n);
             G.Y64a.alloc((size_t)n);
             G.Y64b.alloc((size_t)n);
@@ -605,6 +709,11 @@ extern "C" gksl_status gksl_batch_propagate(gksl_batch *b, const long long *spp,
             double T = 2.0 * M_PI / G.ctx->omega;
             double h = T / (double)spp[i];
             long long n = n_steps[i];
+            if (G.ctx->drive_shape == GKSL_DRIVE_SQUARE) {
+                double k = G.t / h;
+                GK_REQUIRE(spp[i] % 2 == 0 && std::fabs(k - std::nearbyint(k)) <= 1e-6 * std::max(1.0, std::fabs(k)),
+                           GKSL_ERR_ARG, "the square drive needs an even steps_per_period and times on the step grid");
+            }
             if (G.h != h || G.nsteps != n) clear_batch_graphs(b);
             G.h = h;
             G.nsteps = n;
@@ -614,8 +723,8 @@ extern "C" gksl_status gksl_batch_propagate(gksl_batch *b, const long long *spp,
                 clear_batch_graphs(b);
             }
             if (n > 0) {
-                k_sin_table<<<grid_for(n, 256), 256, 0, b->stream>>>(G.t, h, G.ctx->omega, n, G.sin_tab.p,
-                                                                     G.sin_tab_f.p);
+                k_sin_table<<<grid_for(n, 256), 256, 0, b->stream>>>(G.t, h, G.ctx->omega, G.ctx->drive_shape, n,
+                                                                     G.sin_tab.p, G.sin_tab_f.p);
                 GK_LAUNCH_CHECK();
             }
             G.t += (double)n * h;
@@ -656,7 +765,7 @@ extern "C" gksl_status gksl_batch_get_state(gksl_batch *b, int instance, double 
         while (gi + 1 < b->groups.size() && instance >= b->first_instance[gi + 1]) ++gi;
         Group &G = b->groups[gi];
         DBuf<double> col((size_t)G.D);
-        k_column<<<grid_for(G.D, 256), 256, 0, b->stream>>>(G.V64.p, G.D, G.B, instance - b->first_instance[gi],
+        k_column<<<grid_for(G.D, 256), 256, 0, b->stream>>>(G.V64.p, G.D, (int)G.Bs, instance - b->first_instance[gi],
                                                             col.p);
         GK_LAUNCH_CHECK();
         copy_out(v, col.p, sizeof(double) * G.D, b->stream);
@@ -664,10 +773,60 @@ extern "C" gksl_status gksl_batch_get_state(gksl_batch *b, int instance, double 
     });
 }
 
+extern "C" gksl_status gksl_batch_set_scan(gksl_batch *b, int component, const double *theta_b) {
+    return bguarded(b, [&] {
+        GK_REQUIRE(component >= 0 && component < GKSL_MAX_H0 && theta_b, GKSL_ERR_ARG,
+                   "component index out of range or null theta_b");
+        std::vector<double> th((size_t)b->n_instances);
+        GK_CUDA(cudaMemcpy(th.data(), theta_b, sizeof(double) * th.size(), cudaMemcpyDefault));
+        for (double x : th) GK_REQUIRE(std::isfinite(x), GKSL_ERR_ARG, "theta_b must be finite");
+        for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+            Group &G = b->groups[gi];
+            gksl_ctx *c = G.ctx;
+            GK_REQUIRE(c->has_h0[component], GKSL_ERR_ARG, "the scanned component is not set in every group");
+            const CsrR &q = c->QH0[component];
+            CsrR &m = G.m[3];
+            m.rows = q.rows;
+            m.cols = q.cols;
+            m.nnz = q.nnz;
+            m.rowptr.alloc((size_t)q.rows + 1);
+            m.col.alloc((size_t)std::max(1LL, q.nnz));
+            m.val.alloc((size_t)std::max(1LL, q.nnz));
+            GK_CUDA(cudaMemcpyAsync(m.rowptr.p, q.rowptr.p, sizeof(int) * (q.rows + 1), cudaMemcpyDeviceToDevice,
+                                    b->stream));
+            if (q.nnz > 0) {
+                GK_CUDA(cudaMemcpyAsync(m.col.p, q.col.p, sizeof(int) * q.nnz, cudaMemcpyDeviceToDevice, b->stream));
+                GK_CUDA(cudaMemcpyAsync(m.val.p, q.val.p, sizeof(double) * q.nnz, cudaMemcpyDeviceToDevice, b->stream));
+            }
+            G.mf[3].alloc((size_t)std::max(1LL, q.nnz));
+            if (q.nnz > 0) {
+                k_f2<<<grid_for(q.nnz, 256), 256, 0, b->stream>>>(m.val.p, G.mf[3].p, q.nnz);
+                GK_LAUNCH_CHECK();
+            }
+            // instance b uses theta_b in place of the context's theta_k: coefficient theta_b - theta_k
+            std::vector<double> s((size_t)G.B);
+            std::vector<float> sf((size_t)G.B);
+            for (int i = 0; i < G.B; ++i) {
+                s[i] = th[b->first_instance[gi] + i] - c->h0[component].weight;
+                sf[i] = (float)s[i];
+            }
+            G.S.alloc((size_t)G.B);
+            G.Sf.alloc((size_t)G.B);
+            GK_CUDA(cudaMemcpy(G.S.p, s.data(), sizeof(double) * G.B, cudaMemcpyHostToDevice));
+            GK_CUDA(cudaMemcpy(G.Sf.p, sf.data(), sizeof(float) * G.B, cudaMemcpyHostToDevice));
+            G.nch = 4;
+        }
+        GK_CUDA(cudaStreamSynchronize(b->stream));
+        clear_batch_graphs(b);
+        b->tuned = false;
+    });
+}
+
 extern "C" gksl_status gksl_batch_info(gksl_batch *b, int group, int *instances_per_lane, double *tuned_us_per_step) {
     return bguarded(b, [&] {
         GK_REQUIRE(group >= 0 && group < (int)b->groups.size(), GKSL_ERR_ARG, "bad group");
-        if (instances_per_lane) *instances_per_lane = b->groups[group].ipl;
+        // 4 for the 16-byte gather path (4 consecutive instances per lane)
+        if (instances_per_lane) *instances_per_lane = b->groups[group].vec4 ? 4 : b->groups[group].ipl;
         if (tuned_us_per_step) *tuned_us_per_step = b->groups[group].tuned_us;
     });
 }

@@ -155,6 +155,7 @@ struct gksl_ctx {
     gk::Op h1;
     gk::Op diss[GKSL_MAX_P];
     double E = 0.0, A = 0.0, omega = 1.0;
+    int drive_shape = 0;   // GKSL_DRIVE_SIN or GKSL_DRIVE_SQUARE
     bool drive_set = false;
 
     // components (unfolded, unit weight), rebuilt when an operator changes
@@ -358,6 +359,22 @@ __host__ __device__ inline double structure_value(int which, const El &x, const 
 }
 
 // ------------------------------------------------------------------ launch helpers
+
+// theta of the drive eps = E + A theta at the three stage times of the step [tn, tn + h]
+// (square shape: theta at the step midpoint for every stage)
+__host__ __device__ inline void drive_theta(int shape, double omega, double tn, double h, double th[3]) {
+    if (shape == 1) {
+        const double T = 2.0 * 3.14159265358979323846 / omega;
+        double m = fmod(tn + 0.5 * h, T);
+        if (m < 0) m += T;
+        const double s = m < 0.5 * T ? 1.0 : -1.0;
+        th[0] = th[1] = th[2] = s;
+        return;
+    }
+    th[0] = sin(omega * tn);
+    th[1] = sin(omega * (tn + 0.5 * h));
+    th[2] = sin(omega * (tn + h));
+}
 
 inline unsigned grid_for(long long n, int threads) {
     long long g = (n + threads - 1) / threads;

@@ -31,6 +31,8 @@ void clear_graphs(gksl_ctx *c);
 bool state_finite(gksl_ctx *c);
 // drive table eps(t) - E for steps [0, n) of a run starting at t0
 void fill_eps_table(gksl_ctx *c, double t0, double h, long long n);
+// the square drive's jumps must fall on the step grid (even steps/period, time on the grid)
+void check_drive_grid(const gksl_ctx *c, long long spp, double h);
 // `count` RK4 steps on the context state starting at global step `first` (drive table index)
 void advance(gksl_ctx *c, int precision, double h, long long first, long long count);
 // stages 1-3 of step g from y1 (FP64: double*, FP32: float*), writing the stage inputs Y2, Y3, Y4

@@ -26,13 +26,15 @@ constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / 32;
 constexpr int kGraphSteps = 64;
 
-__global__ void k_eps_table(double t0, double h, double A, double omega, long long n, double *__restrict__ tab) {
+__global__ void k_eps_table(double t0, double h, double A, double omega, int shape, long long n,
+                            double *__restrict__ tab) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double tn = t0 + (double)i * h;
-    tab[3 * i + 0] = A * sin(omega * tn);
-    tab[3 * i + 1] = A * sin(omega * (tn + 0.5 * h));
-    tab[3 * i + 2] = A * sin(omega * (tn + h));
+    double th[3];
+    drive_theta(shape, omega, t0 + (double)i * h, h, th);
+    tab[3 * i + 0] = A * th[0];
+    tab[3 * i + 1] = A * th[1];
+    tab[3 * i + 2] = A * th[2];
 }
 
 __global__ void k_set_ll(long long *p, long long v) { *p = v; }
@@ -539,9 +541,18 @@ void fill_eps_table(gksl_ctx *c, double t0, double h, long long n) {
         c->eps_tab.alloc(need);
     }
     if (n > 0) {
-        k_eps_table<<<grid_for(n, 256), 256, 0, c->stream>>>(t0, h, c->A, c->omega, n, c->eps_tab.p);
+        k_eps_table<<<grid_for(n, 256), 256, 0, c->stream>>>(t0, h, c->A, c->omega, c->drive_shape, n,
+                                                              c->eps_tab.p);
         GK_LAUNCH_CHECK();
     }
+}
+
+void check_drive_grid(const gksl_ctx *c, long long spp, double h) {
+    if (c->drive_shape != GKSL_DRIVE_SQUARE) return;
+    GK_REQUIRE(spp % 2 == 0, GKSL_ERR_ARG, "the square drive needs an even steps_per_period (jumps at T/2)");
+    double k = c->t / h;
+    GK_REQUIRE(std::fabs(k - std::nearbyint(k)) <= 1e-6 * std::max(1.0, std::fabs(k)), GKSL_ERR_ARG,
+               "the square drive needs the current time on the step grid");
 }
 
 void advance(gksl_ctx *c, int precision, double h, long long first, long long count) {
@@ -586,6 +597,7 @@ void propagate(gksl_ctx *c, long long spp, long long n_steps, int precision, lon
     ensure_work(c, precision == 32);
     const double T = 2.0 * M_PI / c->omega;
     const double h = T / (double)spp;
+    check_drive_grid(c, spp, h);
     fill_eps_table(c, c->t, h, std::max(n_steps, 8LL));   // the variant timing below uses 8 steps
     DBuf<double> &tab = c->eps_tab;
     if (precision == 32) {

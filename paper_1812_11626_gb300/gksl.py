@@ -61,6 +61,7 @@ _SIGS = {
     "gksl_set_dissipator": (_S, [_P, _I, _D, _P, _P, _P, _P, _I]),
     "gksl_set_gamma": (_S, [_P, _I, _D]),
     "gksl_set_drive": (_S, [_P, _D, _D, _D]),
+    "gksl_set_drive_shape": (_S, [_P, _I]),
     "gksl_expand": (_S, [_P, _P, _P, _P, _P, _I, _P, _P]),
     "gksl_structure_count": (_S, [_I, _I, ctypes.POINTER(_L)]),
     "gksl_structure_enumerate": (_S, [_I, _I, _L, _P, _P, _P, _P, ctypes.POINTER(_L)]),
@@ -83,6 +84,7 @@ _SIGS = {
     "gksl_batch_propagate": (_S, [_P, _P, _P, _L, ctypes.POINTER(_D)]),
     "gksl_batch_get_state": (_S, [_P, _I, _P]),
     "gksl_batch_info": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "gksl_batch_set_scan": (_S, [_P, _I, _P]),
     "gksl_get_info": (_S, [_P, ctypes.POINTER(gksl_info)]),
     "gksl_propagate_csr_noalloc": (_S, [_L, _P, _P, _P, _P, _P, _P, _P, _P, _D, _D, _L, _D, _D, _D, _P]),
 }
@@ -169,6 +171,13 @@ def gksl_set_gamma(ctx, p, gamma):
 
 def gksl_set_drive(ctx, E, A, omega):
     _check(_lib.gksl_set_drive(ctx, E, A, omega), ctx)
+
+
+GKSL_DRIVE_SIN, GKSL_DRIVE_SQUARE = 0, 1
+
+
+def gksl_set_drive_shape(ctx, shape):
+    _check(_lib.gksl_set_drive_shape(ctx, int(shape)), ctx)
 
 
 def gksl_expand(ctx, rowptr, col, re, im, nnz, coef_re, coef_im=None):
@@ -284,6 +293,11 @@ def gksl_batch_get_state(b, instance, v):
     _check(_lib.gksl_batch_get_state(b, int(instance), _ptr(v)), batch=b)
 
 
+def gksl_batch_set_scan(b, component, theta_b):
+    th = np.ascontiguousarray(theta_b, dtype=np.float64)
+    _check(_lib.gksl_batch_set_scan(b, int(component), _ptr(th)), batch=b)
+
+
 def gksl_batch_info(b, group):
     ipl, us = _I(), _D()
     _check(_lib.gksl_batch_info(b, int(group), ctypes.byref(ipl), ctypes.byref(us)), batch=b)
@@ -340,6 +354,72 @@ def dimer_context(d, device=0, stream=None, flags=GKSL_ASM_FP32 | GKSL_ASM_TRANS
         gksl_assemble(ctx, flags)
     gksl_set_rho0(ctx, d.rho0_dense().real.copy(), d.rho0_dense().imag.copy())
     return ctx
+
+
+def dimer_batch(instances, device=0):
+    """Batch of dimer instances (dicts with N, A, gamma): one group per N, group contexts at rate
+    1/(N-1) so that the per-instance scale g_b = gamma_b gives the rate gamma_b/(N-1).
+
+    Returns (batch, contexts, groups) where groups[i] = (N, [instance indices], stable steps per
+    period for the group's largest A and gamma)."""
+    from . import workloads as W
+    by_n = {}
+    for i, x in enumerate(instances):
+        by_n.setdefault(x["N"], []).append(i)
+    ctxs, n_inst, A, g, groups = [], [], [], [], []
+    for N in sorted(by_n):
+        idx = by_n[N]
+        d = W.dimer(N)
+        d.rate = 1.0 / (N - 1)
+        c = dimer_context(d, device=device, flags=GKSL_ASM_FP32)
+        p = d.params
+        gksl_set_drive(c, p["E"], max(instances[i]["A"] for i in idx), p["omega"])
+        gksl_set_gamma(c, 0, max(instances[i]["gamma"] for i in idx) / (N - 1))
+        spp = gksl_min_stable_steps(c)
+        gksl_set_gamma(c, 0, 1.0 / (N - 1))
+        gksl_set_drive(c, p["E"], p["A"], p["omega"])
+        gksl_assemble(c, GKSL_ASM_FP32)
+        ctxs.append(c)
+        n_inst.append(len(idx))
+        A += [instances[i]["A"] for i in idx]
+        g += [instances[i]["gamma"] for i in idx]
+        groups.append((N, idx, spp))
+    return gksl_batch_create(ctxs, n_inst, A, g), ctxs, groups
+
+
+def bifurcation_scan(N, U_values, periods, steps_per_period=None, device=0, params=None):
+    """Populations diag rho(t = periods * T) of the driven dimer for every interaction U in U_values,
+    propagated together as one batch (the quantum bifurcation diagram of Sec. III / Sec. V at
+    t_s = 0 after a transient of `periods` periods).  Returns (populations [len(U), N], spp)."""
+    from . import workloads as W
+    d = W.dimer(N, params)
+    ctx = dimer_context(d, device=device, flags=GKSL_ASM_FP32)
+    b = None
+    try:
+        p = d.params
+        n = len(U_values)
+        if steps_per_period is None:
+            gksl_set_theta(ctx, 1, float(np.max(np.abs(U_values))))
+            steps_per_period = gksl_min_stable_steps(ctx)
+            steps_per_period += steps_per_period % 2
+            gksl_set_theta(ctx, 1, p["U"])
+            gksl_assemble(ctx, GKSL_ASM_FP32)
+        b = gksl_batch_create([ctx], [n], [p["A"]] * n, [1.0] * n)
+        gksl_batch_set_scan(b, 1, U_values)
+        gksl_batch_propagate(b, [steps_per_period], [steps_per_period * periods], steps_per_period)
+        D = N * N - 1
+        pops = np.zeros((n, N))
+        v = np.zeros(D)
+        re, im = np.zeros((N, N)), np.zeros((N, N))
+        for i in range(n):
+            gksl_batch_get_state(b, i, v)
+            gksl_rho(ctx, v, re, im)
+            pops[i] = np.diag(re)
+        return pops, steps_per_period
+    finally:
+        if b is not None:
+            gksl_batch_destroy(b)
+        gksl_destroy(ctx)
 
 
 class TimeAvgObservable:

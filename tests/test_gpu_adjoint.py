@@ -82,6 +82,41 @@ def test_adjoint_vs_finite_differences(G):
         G.gksl_destroy(ctx)
 
 
+def test_adjoint_n200_stable_steps_vs_finite_differences(G):
+    """The adjoint workload's size (N = 200, D = 39 999) at its stable step count: every component
+    of the gradient of the mean of <n1 - n2> over period 1 against central differences
+    (h = 1e-6 relative) of the GPU's own FP64 loss.  Bound: 1e-6 of the gradient's largest
+    component plus the differences' own rounding, 1e-13 |L| / h (the loss is O(N) while single
+    components can be 1e-6 of it, so a per-component relative bound would test the rounding)."""
+    d = W.dimer(200)
+    ctx = G.dimer_context(d)
+    try:
+        S = G.gksl_min_stable_steps(ctx)
+        grad = np.zeros(4)
+        L0 = G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, 1, 64, grad)
+        p = d.params
+        base = dict(A=p["A"], rate=d.rate, J=p["J"], U=p["U"])
+
+        def loss(th):
+            G.gksl_set_drive(ctx, p["E"], th["A"], p["omega"])
+            G.gksl_set_gamma(ctx, 0, th["rate"])
+            G.gksl_set_theta(ctx, 0, th["J"])
+            G.gksl_set_theta(ctx, 1, th["U"])
+            G.gksl_assemble(ctx, G.GKSL_ASM_FP32 | G.GKSL_ASM_TRANSPOSE)
+            return G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, 1, 64, np.zeros(4))
+
+        gmax = np.abs(grad).max()
+        for i, key in enumerate(["A", "rate", "J", "U"]):
+            hfd = 1e-6 * abs(base[key])
+            tp = dict(base); tp[key] += hfd
+            tm = dict(base); tm[key] -= hfd
+            fd = (loss(tp) - loss(tm)) / (2 * hfd)
+            bound = 1e-6 * gmax + 1e-13 * abs(L0) / hfd
+            assert abs(fd - grad[i]) <= bound, (key, fd, grad[i], bound)
+    finally:
+        G.gksl_destroy(ctx)
+
+
 def test_autograd_function(G):
     import torch
     d = W.dimer(5)

@@ -50,6 +50,50 @@ def test_batch_mixed_n_vs_oracle(G):
             G.gksl_destroy(c)
 
 
+def test_batch_256_seeded_instances_sampled(G):
+    """The batched workload at full size (256 seeded instances, N in {50, 100, 200}) in the launch
+    configuration the benchmark times: a tenth of a period per group at its stable step size;
+    three instances of every group against their own oracle runs (FP32 bulk tolerance)."""
+    inst = W.batch_instances(256, 1812)
+    b, ctxs, groups = G.dimer_batch(inst)
+    try:
+        spps = [spp for _, _, spp in groups]
+        steps = [max(1, s // 10) for s in spps]
+        G.gksl_batch_propagate(b, spps, steps, 0)
+        pos = 0
+        for (N, idx, spp), n in zip(groups, steps):
+            for j in (0, len(idx) // 2, len(idx) - 1):
+                x = inst[idx[j]]
+                d = W.dimer(N, dict(A=x["A"], gamma=x["gamma"]))
+                u = SYS.unfold_dimer(d)
+                v_ref, _ = SYS.propagate_dimer(d, u, spp, n)
+                v = np.zeros(N * N - 1)
+                G.gksl_batch_get_state(b, pos + j, v)
+                assert np.abs(v - v_ref).max() < 1e-5, (N, j, np.abs(v - v_ref).max())
+            pos += len(idx)
+    finally:
+        G.gksl_batch_destroy(b)
+        for c in ctxs:
+            G.gksl_destroy(c)
+
+
+def test_bifurcation_scan_vs_oracle(G):
+    """U-scan of the dimer as one batch (a per-instance interaction weight): populations
+    diag rho after 2 periods for 8 values of U against single-instance oracle runs, and the
+    populations are a probability distribution."""
+    N = 12
+    U = np.linspace(0.0, 1.4, 8)
+    pops, spp = G.bifurcation_scan(N, U, periods=2)
+    from oracle import basis as OB
+    for i in (0, 3, 7):
+        d = W.dimer(N, dict(U=float(U[i])))
+        u = SYS.unfold_dimer(d)
+        v_ref, _ = SYS.propagate_dimer(d, u, spp, 2 * spp)
+        ref = np.real(np.diag(OB.rho_from_v(v_ref, N=N)))
+        assert np.abs(pops[i] - ref).max() < 1e-5, (i, np.abs(pops[i] - ref).max())
+    assert np.abs(pops.sum(1) - 1).max() < 1e-12 and pops.min() > -1e-6
+
+
 def test_batch_fp64_correction_only_matches_fp64(G):
     """With an FP64 step every step the batch reproduces the FP64 single-instance path."""
     d = W.dimer(7)

