@@ -83,6 +83,13 @@ gksl_status gksl_set_h1(gksl_ctx *ctx, const int *rowptr, const int *col, const 
  * Tr(L_p)/N is folded into an effective Hamiltonian.  nnz = 0 removes the channel. */
 gksl_status gksl_set_dissipator(gksl_ctx *ctx, int p, double gamma_p, const int *rowptr, const int *col,
                                 const double *re, const double *im, int nnz);
+/* Dissipator given as a Kossakowski matrix A over the generators (Eq. 8): D x D row-major real and
+ * imaginary parts (a_im may be NULL), Hermitian and positive semidefinite, rank <= GKSL_MAX_P,
+ * N <= 64.  A is factorised as sum_p c_p c_p^+ (pivoted Cholesky; pivots <= tol * max diag(A) end
+ * the factorisation) and channel p is set to L_p = sum_j c_pj F_j / |c_p| with gamma_p = |c_p|^2,
+ * replacing every previously set channel.  GKSL_ERR_ARG if A is not Hermitian, not positive
+ * semidefinite, or of higher rank. */
+gksl_status gksl_set_kossakowski(gksl_ctx *ctx, const double *a_re, const double *a_im, double tol);
 /* Change gamma_p of an existing channel without re-expanding it. */
 gksl_status gksl_set_gamma(gksl_ctx *ctx, int p, double gamma_p);
 /* eps(t) = E + A sin(omega t), omega > 0; the period is T = 2 pi / omega (Sec. III). */

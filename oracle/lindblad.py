@@ -42,6 +42,34 @@ def unfold_dense(H, Ls=(), gammas=(), B=None, return_imag=False):
     return Q.real.copy(), K.real.copy()
 
 
+def lindbladian_kossakowski(rho, H, A, B):
+    """Eq. 8 form: -i[H, rho] + sum_jk a_jk (F_j rho F_k^+ - 1/2 {F_k^+ F_j, rho}) for a
+    Kossakowski matrix A over the generators B (the paper's 1/2([F_j, rho F_k^+] + [F_j rho, F_k^+])
+    multiplied out), without decomposing A."""
+    out = -1j * (H @ rho - rho @ H)
+    M = A.shape[0]
+    for j in range(M):
+        for k in range(M):
+            a = A[j, k]
+            if a == 0:
+                continue
+            Fj, Fk = B[j], B[k].conj().T
+            out = out + a * (Fj @ rho @ Fk - 0.5 * (Fk @ Fj @ rho + rho @ Fk @ Fj))
+    return out
+
+
+def unfold_dense_kossakowski(H, A, B=None):
+    """(Q + R, K) of the Eq. 8 Lindbladian by Q_sm = Tr(F_s L(F_m)), K_s = Tr(F_s L(1/N))."""
+    H = np.asarray(H, dtype=np.complex128)
+    N = H.shape[0]
+    if B is None:
+        B = _b.basis(N)
+    LB = np.stack([lindbladian_kossakowski(F, H, A, B) for F in B])
+    Q = np.einsum("sij,mji->sm", B, LB)
+    K = np.einsum("sij,ji->s", B, lindbladian_kossakowski(np.eye(N, dtype=np.complex128) / N, H, A, B))
+    return Q.real.copy(), K.real.copy()
+
+
 def liouvillian_vec(H, Ls=(), gammas=()):
     """N^2 x N^2 matrix of L acting on vec(rho) (column stacking), from Eq. 1.
 

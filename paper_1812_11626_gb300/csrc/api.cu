@@ -293,6 +293,112 @@ extern "C" gksl_status gksl_set_drive(gksl_ctx *c, double E, double A, double om
     });
 }
 
+// Kossakowski matrix -> channels.  A = sum_p c_p c_p^+ by a diagonally pivoted Cholesky
+// factorisation (exact for a positive semidefinite A of rank <= GKSL_MAX_P); then
+// gamma_p = |c_p|^2, l_p = c_p / |c_p|, L_p = sum_j l_pj F_j.  Any such rank factorisation gives
+// the same Lindbladian as the eigen-decomposition of Eq. 9 (the dissipator is invariant under a
+// unitary remixing of its channels).
+extern "C" gksl_status gksl_set_kossakowski(gksl_ctx *c, const double *a_re, const double *a_im, double tol) {
+    return guarded(c, [&] {
+        GK_REQUIRE(a_re && tol >= 0.0, GKSL_ERR_ARG, "a_re must not be null and tol >= 0");
+        const long long D = c->D;
+        GK_REQUIRE(D <= 4095, GKSL_ERR_ARG, "the Kossakowski form is limited to N <= 64");
+        const int N = c->N;
+        size_t DD = (size_t)D * D;
+        std::vector<double> ar = to_host(a_re, DD, c->stream), ai = a_im ? to_host(a_im, DD, c->stream)
+                                                                         : std::vector<double>(DD, 0.0);
+        double mx = 0.0;
+        for (size_t i = 0; i < DD; ++i) {
+            GK_REQUIRE(std::isfinite(ar[i]) && std::isfinite(ai[i]), GKSL_ERR_ARG, "non-finite Kossakowski entry");
+            mx = std::max(mx, std::hypot(ar[i], ai[i]));
+        }
+        for (long long j = 0; j < D; ++j)
+            for (long long k = 0; k < D; ++k)
+                GK_REQUIRE(std::fabs(ar[j * D + k] - ar[k * D + j]) <= 1e-12 * mx &&
+                               std::fabs(ai[j * D + k] + ai[k * D + j]) <= 1e-12 * mx,
+                           GKSL_ERR_ARG, "Kossakowski matrix is not Hermitian");
+        // pivoted Cholesky on the residual R = A - sum c c^+
+        std::vector<double> rr = ar, ri = ai;
+        std::vector<std::vector<double>> cr, ci;
+        double dmax0 = 0.0;
+        for (long long j = 0; j < D; ++j) dmax0 = std::max(dmax0, rr[j * D + j]);
+        const double thr = tol * std::max(dmax0, 1e-300);
+        for (;;) {
+            long long piv = -1;
+            double best = thr;
+            for (long long j = 0; j < D; ++j)
+                if (rr[j * D + j] > best) { best = rr[j * D + j]; piv = j; }
+            if (piv < 0) break;
+            GK_REQUIRE((int)cr.size() < GKSL_MAX_P, GKSL_ERR_ARG,
+                       "Kossakowski matrix has rank above the channel limit (8)");
+            double s = 1.0 / std::sqrt(best);
+            std::vector<double> vr((size_t)D), vi((size_t)D);
+            for (long long i = 0; i < D; ++i) {   // c = R[:, piv] / sqrt(R[piv, piv])
+                vr[i] = rr[i * D + piv] * s;
+                vi[i] = ri[i * D + piv] * s;
+            }
+            for (long long i = 0; i < D; ++i)
+                for (long long k = 0; k < D; ++k) {   // R -= c c^+
+                    rr[i * D + k] -= vr[i] * vr[k] + vi[i] * vi[k];
+                    ri[i * D + k] -= vi[i] * vr[k] - vr[i] * vi[k];
+                }
+            cr.push_back(std::move(vr));
+            ci.push_back(std::move(vi));
+        }
+        for (long long j = 0; j < D; ++j)
+            GK_REQUIRE(rr[j * D + j] >= -std::max(thr, 1e-12 * dmax0), GKSL_ERR_ARG,
+                       "Kossakowski matrix is not positive semidefinite");
+        // channels L_p = sum_j l_pj F_j as dense N x N matrices, then CSR
+        Basis B(N);
+        const double r2 = GK_RSQRT2;
+        for (int p = 0; p < GKSL_MAX_P; ++p) {
+            if (p >= (int)cr.size()) {
+                if (c->diss[p].set) {
+                    c->diss[p] = Op();
+                    c->comp_dirty = true;
+                    c->assembled = false;
+                }
+                continue;
+            }
+            double g = 0.0;
+            for (long long j = 0; j < D; ++j) g += cr[p][j] * cr[p][j] + ci[p][j] * ci[p][j];
+            double inv = 1.0 / std::sqrt(g);
+            std::vector<double> Lr((size_t)N * N, 0.0), Li((size_t)N * N, 0.0);
+            for (long long j = 0; j < D; ++j) {
+                double xr = cr[p][j] * inv, xi = ci[p][j] * inv;
+                if (xr == 0.0 && xi == 0.0) continue;
+                El e = B.decode(j);
+                if (e.kind == 0) {          // S: 1/sqrt2 at (a,b), (b,a)
+                    Lr[e.a * N + e.b] += xr * r2; Li[e.a * N + e.b] += xi * r2;
+                    Lr[e.b * N + e.a] += xr * r2; Li[e.b * N + e.a] += xi * r2;
+                } else if (e.kind == 1) {   // J: -i/sqrt2 at (a,b), +i/sqrt2 at (b,a)
+                    Lr[e.a * N + e.b] += xi * r2; Li[e.a * N + e.b] -= xr * r2;
+                    Lr[e.b * N + e.a] -= xi * r2; Li[e.b * N + e.a] += xr * r2;
+                } else {                    // D^l: c_l on k < l, -l c_l at l
+                    for (int k = 0; k <= e.a; ++k) {
+                        double dk = dl_diag(e.a, k);
+                        Lr[k * N + k] += xr * dk;
+                        Li[k * N + k] += xi * dk;
+                    }
+                }
+            }
+            std::vector<int> rp((size_t)N + 1, 0), cc;
+            std::vector<double> vr, vi;
+            for (int r = 0; r < N; ++r) {
+                for (int k = 0; k < N; ++k)
+                    if (Lr[r * N + k] != 0.0 || Li[r * N + k] != 0.0) {
+                        cc.push_back(k);
+                        vr.push_back(Lr[r * N + k]);
+                        vi.push_back(Li[r * N + k]);
+                    }
+                rp[r + 1] = (int)cc.size();
+            }
+            set_op(c, c->diss[p], rp.data(), cc.data(), vr.data(), vi.data(), (int)cc.size(), false);
+            c->diss[p].weight = g;
+        }
+    });
+}
+
 extern "C" gksl_status gksl_set_drive_shape(gksl_ctx *c, int shape) {
     return guarded(c, [&] {
         GK_REQUIRE(shape == GKSL_DRIVE_SIN || shape == GKSL_DRIVE_SQUARE, GKSL_ERR_ARG, "unknown drive shape");

@@ -62,6 +62,7 @@ _SIGS = {
     "gksl_set_gamma": (_S, [_P, _I, _D]),
     "gksl_set_drive": (_S, [_P, _D, _D, _D]),
     "gksl_set_drive_shape": (_S, [_P, _I]),
+    "gksl_set_kossakowski": (_S, [_P, _P, _P, _D]),
     "gksl_expand": (_S, [_P, _P, _P, _P, _P, _I, _P, _P]),
     "gksl_structure_count": (_S, [_I, _I, ctypes.POINTER(_L)]),
     "gksl_structure_enumerate": (_S, [_I, _I, _L, _P, _P, _P, _P, ctypes.POINTER(_L)]),
@@ -178,6 +179,11 @@ GKSL_DRIVE_SIN, GKSL_DRIVE_SQUARE = 0, 1
 
 def gksl_set_drive_shape(ctx, shape):
     _check(_lib.gksl_set_drive_shape(ctx, int(shape)), ctx)
+
+
+def gksl_set_kossakowski(ctx, a_re, a_im=None, tol=1e-12):
+    a_re, a_im = _arr(a_re, np.float64), _arr(a_im, np.float64)
+    _check(_lib.gksl_set_kossakowski(ctx, _ptr(a_re), _ptr(a_im), float(tol)), ctx)
 
 
 def gksl_expand(ctx, rowptr, col, re, im, nnz, coef_re, coef_im=None):

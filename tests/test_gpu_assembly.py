@@ -174,6 +174,59 @@ def test_assembly_dimer_n1000_full(G):
         G.gksl_destroy(ctx)
 
 
+def test_kossakowski_matrix_vs_eq8(G):
+    """General dissipator from a rank-3 Kossakowski matrix (Eq. 8) against the oracle's Eq. 8 applied
+    with A directly; a rank-9 matrix and an indefinite one are rejected."""
+    N = 5
+    M = N * N - 1
+    rng = np.random.default_rng(21)
+    H = W.random_operator(N, 0.6, 77, hermitian=True)
+    C = rng.normal(size=(M, 3)) + 1j * rng.normal(size=(M, 3))
+    A = C @ C.conj().T * 0.05
+    ctx = G.gksl_create(N)
+    try:
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 1.0, op=H)
+        G.gksl_set_drive(ctx, 0.0, 0.0, 1.0)
+        G.gksl_set_kossakowski(ctx, A.real.copy(), A.imag.copy())
+        G.gksl_assemble(ctx, 0)
+        Qr, Kr = OL.unfold_dense_kossakowski(H.to_dense(), A)
+        assert rel_err(csr_of(G, ctx, G.GKSL_MAT_Q0).toarray(), Qr) < TOL_ASM
+        K = np.zeros(M)
+        G.gksl_get_k(ctx, K)
+        assert np.abs(K - Kr).max() < TOL_ASM * np.abs(Qr).max()
+        C9 = rng.normal(size=(M, 9)) + 1j * rng.normal(size=(M, 9))
+        A9 = C9 @ C9.conj().T
+        with pytest.raises(G.GkslError):
+            G.gksl_set_kossakowski(ctx, A9.real.copy(), A9.imag.copy())
+        Aneg = A.copy()
+        Aneg[0, 0] -= 10 * np.abs(A).max()
+        with pytest.raises(G.GkslError):
+            G.gksl_set_kossakowski(ctx, Aneg.real.copy(), Aneg.imag.copy())
+    finally:
+        G.gksl_destroy(ctx)
+
+
+@pytest.mark.parametrize("N", [12, 16])
+def test_dense_operators_vs_brute_force(G, N):
+    """Fully dense H and a dense non-Hermitian L (the dense column of Table II): assembly against the
+    brute-force definition."""
+    H = W.random_operator(N, 1.0, 300 + N, hermitian=True)
+    L = W.random_operator(N, 1.0, 400 + N)
+    ctx = G.gksl_create(N)
+    try:
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 1.0, op=H)
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, 0.2, op=L)
+        G.gksl_set_drive(ctx, 0.0, 0.0, 1.0)
+        G.gksl_assemble(ctx, 0)
+        Qr, Kr = OL.unfold_dense(H.to_dense(), [L.to_dense()], [0.2])
+        assert rel_err(csr_of(G, ctx, G.GKSL_MAT_Q0).toarray(), Qr) < TOL_ASM
+        K = np.zeros(N * N - 1)
+        G.gksl_get_k(ctx, K)
+        assert np.abs(K - Kr).max() < TOL_ASM * np.abs(Qr).max()
+    finally:
+        G.gksl_destroy(ctx)
+
+
 # ------------------------------------------------------------ state, rho, observables (Eq. 6)
 
 def test_rho0_rho_and_observable(G):

@@ -167,6 +167,25 @@ def test_paper_formulas_reproduce_definition(N):
     assert np.abs(Qn - Q).max() > 1e-6 * scale
 
 
+def test_kossakowski_form_reduces_to_jump_operators():
+    """Eq. 8 with A = sum_p gamma_p l_p l_p^+ (Eq. 9) equals the jump-operator form with
+    L_p = sum_j l_pj F_j (Eq. 1), for a rank-2 A."""
+    N = 3
+    F = B.basis(N)
+    rng = np.random.default_rng(12)
+    H = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    H = H + H.conj().T
+    M = N * N - 1
+    ls = [rng.normal(size=M) + 1j * rng.normal(size=M) for _ in range(2)]
+    gs = [0.4, 1.3]
+    A = sum(g * np.outer(l, l.conj()) for g, l in zip(gs, ls))
+    Qa, Ka = Lb.unfold_dense_kossakowski(H, A, F)
+    Ls = [np.einsum("j,jab->ab", l, F) for l in ls]
+    Ql, Kl = Lb.unfold_dense(H, Ls, gs, F)
+    assert np.abs(Qa - Ql).max() < 1e-13 * np.abs(Ql).max()
+    assert np.abs(Ka - Kl).max() < 1e-13 * np.abs(Ql).max()
+
+
 @pytest.mark.parametrize("N", [3, 6])
 def test_hamiltonian_part_skew(N):
     """Eq. 7: Q from the Hamiltonian alone is skew-symmetric."""
