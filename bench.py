@@ -206,6 +206,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case for ncu: N=1000 assembly, then 50 FP64 and 50 FP32 RK4 steps")
+    ap.add_argument("--profile-mf", action="store_true",
+                    help="profiling case for ncu: the N=1000 matrix-free form, 20 FP64 and 20 FP32 RK4 steps")
     ap.add_argument("--profile-batch", action="store_true",
                     help="profiling case for ncu: the 256-instance batch, 40 steps per group")
     args = ap.parse_args()
@@ -218,6 +220,9 @@ def main():
         return
     if args.profile_batch:
         run_profile_batch()
+        return
+    if args.profile_mf:
+        run_profile_mf()
         return
 
     import torch
@@ -325,6 +330,7 @@ def main():
             for i, p in enumerate(("fp64", "fp32"))}
     G.gksl_destroy(ctx)
     if not args.no_extras and rank == 0:
+        extras["matrix_free"] = matrix_free_extras(G, W, torch, stream, d, spp, args.steps)
         extras.update(batched_and_adjoint(G, W, torch))
 
     if rank == 0:
@@ -342,6 +348,65 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def mf_stage_bytes(D, precision):
+    """Compulsory bytes per matrix-free stage launch, averaged over the 4 stages of a step: the
+    same 17 vector passes as the CSR stages (plus the FP64 master update of the FP32 form) and no
+    matrix stream; the O(N) band data and the diagonal of rho are noise at N = 1000."""
+    vb = 8 if precision == 64 else 4
+    return (17 * vb * D + (16 * D if precision == 32 else 0)) / 4.0
+
+
+def matrix_free_extras(G, W, torch, stream, d, spp, steps):
+    """The matrix-free form (Q applied on the fly) on the same N = 1000 workload: FP64 and FP32
+    RK4 steps/s, the bytes it streams, and its distance to the CSR FP64 path after 2000 steps."""
+    ctx = G.dimer_context(d, stream=stream.cuda_stream, flags=G.GKSL_ASM_MATRIX_FREE | G.GKSL_ASM_FP32,
+                          assemble=False)
+    out = {"assembly_s": G.gksl_assemble(ctx, G.GKSL_ASM_MATRIX_FREE | G.GKSL_ASM_FP32)}
+    D = d.N * d.N - 1
+    out["device_bytes"] = G.gksl_get_info(ctx).device_bytes
+    for prec in (64, 32):
+        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+        G.gksl_propagate(ctx, spp, STEP_RK4, prec, 0, 0, None)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            G.gksl_propagate(ctx, spp, STEP_RK4, prec, 0, 0, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        us_launch = 1e3 * ms / (steps * STEP_RK4 * 4)
+        out["fp%d" % prec] = {"value": steps * STEP_RK4 / (ms * 1e-3), "unit": UNIT, "us_per_stage": us_launch,
+                              "algorithmic_bytes_per_launch": mf_stage_bytes(D, prec),
+                              "achieved_gbs": mf_stage_bytes(D, prec) / (us_launch * 1e-6) / 1e9}
+    # distance to the CSR FP64 path after STEP_RK4 FP64 steps from rho0
+    ref = G.dimer_context(d, stream=stream.cuda_stream, flags=0)
+    va, vb = np.zeros((1, D)), np.zeros((1, D))
+    G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+    G.gksl_propagate(ctx, spp, STEP_RK4, 64, 0, STEP_RK4, va)
+    G.gksl_propagate(ref, spp, STEP_RK4, 64, 0, STEP_RK4, vb)
+    out["max_abs_diff_vs_csr_fp64"] = float(np.abs(va - vb).max())
+    G.gksl_destroy(ref)
+    G.gksl_destroy(ctx)
+    return out
+
+
+def run_profile_mf():
+    """Small, fixed case for ncu: the N = 1000 matrix-free form (vectors only, about 60 MB on the
+    device; the 8 MB state vectors fit L2, so DRAM counters read low), 20 FP64 then 20 FP32 steps."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1812_11626_gb300 import gksl as G
+    from paper_1812_11626_gb300 import workloads as W
+    d = W.dimer(N_BENCH)
+    ctx = G.dimer_context(d, flags=G.GKSL_ASM_MATRIX_FREE | G.GKSL_ASM_FP32)
+    spp = G.gksl_min_stable_steps(ctx)
+    G.gksl_propagate(ctx, spp, 20, 64, 0, 0, None)
+    G.gksl_propagate(ctx, spp, 20, 32, 0, 0, None)
+    print(json.dumps({"profile_case": "matrix-free N=1000", "steps_per_period": spp}), flush=True)
+    G.gksl_destroy(ctx)
 
 
 def run_profile_case():

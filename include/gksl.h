@@ -130,6 +130,13 @@ gksl_status gksl_structure_enumerate(int N, int which, long long capacity, int *
 #define GKSL_ASM_FP32 1u        /* also build the FP32 copies used by precision 32 */
 #define GKSL_ASM_TRANSPOSE 2u   /* also build the transposes used by the adjoint */
 #define GKSL_ASM_NO_DROP 4u     /* keep entries |q| <= 64 eps max|Q| in Q0 */
+/* Matrix-free form: build no CSR matrix; keep H0 (+ E H1), H1, Gamma = 1/2 sum_p gamma_p L_p^+ L_p
+ * and sqrt(gamma_p) L_p as complex diagonals (O(N) data) and let gksl_propagate apply Q(t) v + K on
+ * the fly, as Tr(F_s L_t(rho)) with rho = 1/N + sum v F (Eq. 1, 6, 8), from tiles of rho rebuilt
+ * from v in shared memory.  Every operator must be banded with half-bandwidth <= 4 (else
+ * GKSL_ERR_ARG).  Excludes GKSL_ASM_TRANSPOSE; gksl_get_csr, gksl_get_k*, the adjoint and the
+ * batched form need a CSR assembly and return GKSL_ERR_STATE. */
+#define GKSL_ASM_MATRIX_FREE 8u
 
 /* Build Q(H0_k), Q(H1), R_p, K_p on the device from the structure constants (Eq. 7, 10, 11),
  * then Q0, Q1 and K.  `seconds` (may be NULL) receives the wall time of the call. */

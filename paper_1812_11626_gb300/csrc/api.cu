@@ -476,6 +476,7 @@ extern "C" gksl_status gksl_get_csr(gksl_ctx *c, int which, long long *nnz, int 
     return guarded(c, [&] {
         GK_REQUIRE(nnz, GKSL_ERR_ARG, "nnz must not be null");
         GK_REQUIRE(c->assembled, GKSL_ERR_STATE, "gksl_assemble must be called first");
+        GK_REQUIRE(!(c->asm_flags & GKSL_ASM_MATRIX_FREE), GKSL_ERR_STATE, "assembled matrix-free: no CSR matrix");
         const CsrR *m = nullptr;
         if (which == GKSL_MAT_Q0) m = &c->Q0;
         else if (which == GKSL_MAT_Q1) m = &c->Q1;
@@ -492,6 +493,7 @@ extern "C" gksl_status gksl_get_k(gksl_ctx *c, double *K) {
     return guarded(c, [&] {
         GK_REQUIRE(K, GKSL_ERR_ARG, "K must not be null");
         GK_REQUIRE(c->assembled, GKSL_ERR_STATE, "gksl_assemble must be called first");
+        GK_REQUIRE(!(c->asm_flags & GKSL_ASM_MATRIX_FREE), GKSL_ERR_STATE, "assembled matrix-free: no K vector");
         copy_out(K, c->K.p, sizeof(double) * c->D, c->stream);
     });
 }
@@ -500,6 +502,7 @@ extern "C" gksl_status gksl_get_k_channel(gksl_ctx *c, int p, double *K) {
     return guarded(c, [&] {
         GK_REQUIRE(K, GKSL_ERR_ARG, "K must not be null");
         GK_REQUIRE(c->assembled, GKSL_ERR_STATE, "gksl_assemble must be called first");
+        GK_REQUIRE(!(c->asm_flags & GKSL_ASM_MATRIX_FREE), GKSL_ERR_STATE, "assembled matrix-free: no K vector");
         GK_REQUIRE(p >= 0 && p < GKSL_MAX_P && c->has_r[p], GKSL_ERR_ARG, "channel not set");
         copy_out(K, c->Kp[p].p, sizeof(double) * c->D, c->stream);
     });
@@ -648,6 +651,10 @@ extern "C" gksl_status gksl_get_info(gksl_ctx *c, gksl_info *out) {
         for (int k = 0; k < GKSL_MAX_H0; ++k) b += c->QH0[k].bytes();
         for (int p = 0; p < GKSL_MAX_P; ++p) b += c->R[p].bytes() + c->Kp[p].bytes();
         for (int i = 0; i < c->adj_n; ++i) b += c->adj[i].bytes() + c->adjf[i].bytes();
+        const MfBands &m = c->mf;
+        b += m.h0.bytes() + m.h1.bytes() + m.g.bytes() + m.l.bytes() + m.r32.bytes() + m.h1o32.bytes() +
+             m.dg32.bytes() + m.lo32.bytes() + m.ld32.bytes() + m.tiles.bytes();
+        for (int i = 0; i < 4; ++i) b += m.img64[i].bytes() + m.img32[i].bytes();
         out->device_bytes = (long long)b;
         out->assemble_seconds = c->assemble_seconds;
         out->max_abs_q0 = c->max_abs_q0;

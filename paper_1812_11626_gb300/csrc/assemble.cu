@@ -514,6 +514,32 @@ void assemble(gksl_ctx *c, unsigned flags) {
     for (int k = 0; k < GKSL_MAX_H0; ++k) any = any || c->h0[k].set;
     for (int p = 0; p < GKSL_MAX_P; ++p) any = any || c->diss[p].set;
     GK_REQUIRE(any, GKSL_ERR_STATE, "no operator set before gksl_assemble");
+    if (flags & GKSL_ASM_MATRIX_FREE) {
+        GK_REQUIRE(!(flags & GKSL_ASM_TRANSPOSE), GKSL_ERR_ARG,
+                   "GKSL_ASM_MATRIX_FREE excludes GKSL_ASM_TRANSPOSE (the adjoint needs CSR matrices)");
+        c->Q0 = CsrR();
+        c->K.release();
+        c->hyb0 = Hyb<double>();
+        c->hyb1 = Hyb<double>();
+        c->hyb0f = Hyb<float>();
+        c->hyb1f = Hyb<float>();
+        for (int i = 0; i < gksl_ctx::kMaxCh; ++i) {
+            c->adj[i] = Hyb<double>();
+            c->adjf[i] = Hyb<float>();
+        }
+        c->has_adj = false;
+        c->adj_n = 0;
+        c->nnz_q0e = 0;
+        c->max_abs_q0 = 0.0;
+        mf_build(c, (flags & GKSL_ASM_FP32) != 0);
+        c->asm_flags = flags;
+        c->assembled = true;
+        c->rk4_tuned[0] = c->rk4_tuned[1] = false;
+        clear_graphs(c);
+        c->assemble_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return;
+    }
+    c->mf = MfBands();
     if (c->comp_dirty) {
         for (int k = 0; k < GKSL_MAX_H0; ++k) {
             c->has_h0[k] = c->h0[k].set;

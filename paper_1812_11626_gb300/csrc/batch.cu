@@ -565,6 +565,8 @@ extern "C" gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, 
         for (int i = 0; i < n_groups; ++i) {
             GK_REQUIRE(groups[i] && n_inst[i] > 0, GKSL_ERR_ARG, "every group needs a context and >= 1 instance");
             GK_REQUIRE(groups[i]->assembled, GKSL_ERR_STATE, "group contexts must be assembled");
+            GK_REQUIRE(!(groups[i]->asm_flags & GKSL_ASM_MATRIX_FREE), GKSL_ERR_STATE,
+                       "group contexts must be assembled with CSR matrices");
             GK_REQUIRE(groups[i]->device == b->device, GKSL_ERR_ARG, "all groups must live on one device");
             total += n_inst[i];
         }

@@ -128,6 +128,27 @@ inline HybView<VT> view(const Hyb<VT> &h) {
     return HybView<VT>{h.ell_col.p, h.ell_val.p, h.ld, h.width, h.tail_ptr.p, h.tail_col.p, h.tail_val.p};
 }
 
+// Band data of the matrix-free form: the operators of L(rho) as complex diagonals, row-major
+// [N][2B+1] with entry (j, d + B) = X_(j, j+d), interleaved (re, im).
+struct MfBands {
+    bool ready = false;
+    int bh = 0, bg = 0, bl = 0;   // half-bandwidths of the instantiation (H, Gamma, L)
+    int P = 0;                    // channels
+    bool real = false;            // every band real
+    int n_tiles = 0, n_diag = 0;  // upper-triangle tiles, of which on the diagonal
+    // FP64 stages: H0 + E H1 (+ sum theta_k H0_k), H1, Gamma = 1/2 sum gamma L^+L, L' = sqrt(gamma) L
+    DBuf<double> h0, h1, g, l;
+    // FP32 stages (diagonals split off, off-diagonal couplings combined in FP64 first):
+    // r: R_(j,a) for a != j; h1o: H1 off the diagonal; dg: H0_jj, H1_jj (hi/lo), 1/2 sum_p off_pj;
+    // lo: L'_p off the diagonal; ld: L'_p,jj (hi/lo of re, im)
+    DBuf<float> r32, h1o32, dg32, lo32, ld32;
+    DBuf<int> tiles;              // (tile row, tile column) per block
+    // diagonal images sqrt(2) sum_l y_l (D^l)_jj of v, yA, yB, acc during a run of steps
+    // (FP64 stages and the FP64 master of the FP32 form; FP32 stages)
+    DBuf<double> img64[4];
+    DBuf<float> img32[4];
+};
+
 // An N x N input operator copied to the device (CSR, complex).
 struct Op {
     bool set = false;
@@ -176,6 +197,7 @@ struct gksl_ctx {
     long long nnz_q0e = 0;
     gk::Hyb<double> hyb0, hyb1;   // propagation format of [Q0 + E Q1 | K] and Q1
     gk::Hyb<float> hyb0f, hyb1f;  // FP32 copies
+    gk::MfBands mf;               // matrix-free form (GKSL_ASM_MATRIX_FREE)
     // adjoint: one channel per parameter matrix, transposed (Q(H)^T = -Q(H) is stored negated),
     // all channels sharing one long-row set: H0 components, then Q1, then the dissipators
     static constexpr int kMaxCh = GKSL_MAX_H0 + 1 + GKSL_MAX_P;

@@ -39,6 +39,14 @@ void advance(gksl_ctx *c, int precision, double h, long long first, long long co
 void forward_stage_inputs(gksl_ctx *c, int precision, double h, long long g, void *y1, void *Y2, void *Y3, void *Y4);
 void to_f32(const double *v, float *o, long long n, cudaStream_t s);
 
+// ---- mfree.cu (matrix-free stages, GKSL_ASM_MATRIX_FREE)
+void mf_build(gksl_ctx *c, bool fp32);
+// diagonal image of the state's D coefficients before a run of steps, and back after it
+void mf_prep(gksl_ctx *c, int precision);
+void mf_post(gksl_ctx *c, int precision);
+// the four stages of one RK4 step
+void mf_step(gksl_ctx *c, int precision, double h, const double *tab, long long local);
+
 // ---- adjoint.cu
 void adjoint_timeavg(gksl_ctx *c, const double *o_diag_dev, long long spp, long long period, int precision,
                      double *loss, double *grad, int n_grad);

@@ -17,6 +17,7 @@
 
 #include "internal.cuh"
 #include "prim.cuh"
+#include "stage.cuh"
 
 namespace gk {
 
@@ -81,40 +82,6 @@ __device__ inline AT tail_dot(const HybView<VT> &H, long long i, int lane, const
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
-}
-
-template <int STAGE>
-__device__ inline int eps_slot() { return STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1); }
-
-// step-size constants, computed once on the host (no per-thread FP64 division)
-struct HConst {
-    double h, h2, h6;   // h, h/2, h/6
-    float hf, h2f, h6f;
-};
-
-// ---- FP64 epilogue
-template <int STAGE>
-__device__ inline void epi64(long long r, double k, double *v, double *__restrict__ yn, double *__restrict__ acc,
-                             const HConst &c) {
-    if (STAGE == 1) { yn[r] = v[r] + c.h2 * k; acc[r] = k; }
-    if (STAGE == 2) { yn[r] = v[r] + c.h2 * k; acc[r] = acc[r] + 2.0 * k; }
-    if (STAGE == 3) { yn[r] = v[r] + c.h * k; acc[r] = acc[r] + 2.0 * k; }
-    if (STAGE == 4) { v[r] = v[r] + c.h6 * (acc[r] + k); }
-}
-
-// ---- FP32 epilogue (v32: FP32 mirror, v64: master)
-template <int STAGE>
-__device__ inline void epi32(long long r, float k, float *v32, double *v64, float *__restrict__ yn,
-                             float *__restrict__ acc, const HConst &c) {
-    if (STAGE == 1) { yn[r] = v32[r] + c.h2f * k; acc[r] = k; }
-    if (STAGE == 2) { yn[r] = v32[r] + c.h2f * k; acc[r] = acc[r] + 2.0f * k; }
-    if (STAGE == 3) { yn[r] = v32[r] + c.hf * k; acc[r] = acc[r] + 2.0f * k; }
-    if (STAGE == 4) {
-        float inc = c.h6f * (acc[r] + k);
-        double nv = v64[r] + (double)inc;
-        v64[r] = nv;
-        v32[r] = (float)nv;
-    }
 }
 
 struct StepArgs {
@@ -183,41 +150,6 @@ __global__ void __launch_bounds__(kThreads) k_stage32(HybView<float> A0, HybView
 }
 
 // ---- variants of the ELL part (same arithmetic, same summation order per row)
-
-template <typename VT>
-struct Vec2;
-template <>
-struct Vec2<double> { using T = double2; };
-template <>
-struct Vec2<float> { using T = float2; };
-
-template <int STAGE, typename VT>
-__device__ inline void epi(long long r, VT k, VT *v, double *v64, VT *__restrict__ yn, VT *__restrict__ acc,
-                           const HConst &hc);
-template <>
-__device__ inline void epi<1, double>(long long r, double k, double *v, double *, double *yn, double *acc,
-                                      const HConst &hc) { epi64<1>(r, k, v, yn, acc, hc); }
-template <>
-__device__ inline void epi<2, double>(long long r, double k, double *v, double *, double *yn, double *acc,
-                                      const HConst &hc) { epi64<2>(r, k, v, yn, acc, hc); }
-template <>
-__device__ inline void epi<3, double>(long long r, double k, double *v, double *, double *yn, double *acc,
-                                      const HConst &hc) { epi64<3>(r, k, v, yn, acc, hc); }
-template <>
-__device__ inline void epi<4, double>(long long r, double k, double *v, double *, double *yn, double *acc,
-                                      const HConst &hc) { epi64<4>(r, k, v, yn, acc, hc); }
-template <>
-__device__ inline void epi<1, float>(long long r, float k, float *v, double *v64, float *yn, float *acc,
-                                     const HConst &hc) { epi32<1>(r, k, v, v64, yn, acc, hc); }
-template <>
-__device__ inline void epi<2, float>(long long r, float k, float *v, double *v64, float *yn, float *acc,
-                                     const HConst &hc) { epi32<2>(r, k, v, v64, yn, acc, hc); }
-template <>
-__device__ inline void epi<3, float>(long long r, float k, float *v, double *v64, float *yn, float *acc,
-                                     const HConst &hc) { epi32<3>(r, k, v, v64, yn, acc, hc); }
-template <>
-__device__ inline void epi<4, float>(long long r, float k, float *v, double *v64, float *yn, float *acc,
-                                     const HConst &hc) { epi32<4>(r, k, v, v64, yn, acc, hc); }
 
 template <int STAGE, typename VT>
 __device__ inline bool long_rows_part(const HybView<VT> &A0, const HybView<VT> &A1, const StepArgs &a, VT eps,
@@ -389,6 +321,10 @@ void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h
 }
 
 void launch_step(gksl_ctx *c, int precision, double h, const double *tab, long long local) {
+    if (c->asm_flags & GKSL_ASM_MATRIX_FREE) {
+        mf_step(c, precision, h, tab, local);
+        return;
+    }
     Launch L = make_launch(c, c->hyb0, h, tab, local);
     int W = c->hyb0.width;
     int var = c->rk4_var[precision == 64 ? 0 : 1];
@@ -419,6 +355,7 @@ void tune_variant(gksl_ctx *c, int precision, double h, const double *tab) {
     int pi = precision == 64 ? 0 : 1;
     if (c->rk4_tuned[pi]) return;
     c->rk4_tuned[pi] = true;
+    if (c->asm_flags & GKSL_ASM_MATRIX_FREE) return;   // one matrix-free kernel per stage
     const char *env = getenv("GKSL_RK4_VARIANT");
     if (env && env[0] >= '0' && env[0] <= '2') {
         c->rk4_var[pi] = env[0] - '0';
@@ -464,8 +401,11 @@ cudaGraphExec_t graph_for(gksl_ctx *c, long long steps, int precision, double h,
     for (auto &g : c->graphs)
         if (g.steps == steps && g.precision == precision && g.h == h && g.variant == var) return g.exec;
     cudaGraph_t graph;
+    const bool mf = (c->asm_flags & GKSL_ASM_MATRIX_FREE) != 0;
     GK_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    if (mf) mf_prep(c, precision);
     for (long long i = 0; i < steps; ++i) launch_step(c, precision, h, tab, i);
+    if (mf) mf_post(c, precision);
     GK_CUDA(cudaStreamEndCapture(c->stream, &graph));
     cudaGraphExec_t exec;
     GK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
@@ -485,7 +425,10 @@ void run_steps(gksl_ctx *c, int precision, double h, const double *tab, long lon
     if (n < end) {
         k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, n);
         GK_LAUNCH_CHECK();
+        const bool mf = (c->asm_flags & GKSL_ASM_MATRIX_FREE) != 0;
+        if (mf) mf_prep(c, precision);
         for (long long i = 0; n + i < end; ++i) launch_step(c, precision, h, tab, i);
+        if (mf) mf_post(c, precision);
         n = end;
     }
 }

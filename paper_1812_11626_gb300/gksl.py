@@ -20,7 +20,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_OOM", "ERR_STATE", "ERR_UNSTAB
 GKSL_MAX_H0 = 8
 GKSL_MAX_P = 8
 GKSL_STRUCT_F, GKSL_STRUCT_D = 0, 1
-GKSL_ASM_FP32, GKSL_ASM_TRANSPOSE, GKSL_ASM_NO_DROP = 1, 2, 4
+GKSL_ASM_FP32, GKSL_ASM_TRANSPOSE, GKSL_ASM_NO_DROP, GKSL_ASM_MATRIX_FREE = 1, 2, 4, 8
 GKSL_MAT_Q0, GKSL_MAT_Q1, GKSL_MAT_H0, GKSL_MAT_R = 0, 1, 16, 32
 
 if not os.path.exists(LIB_PATH):

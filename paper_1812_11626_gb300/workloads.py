@@ -169,3 +169,17 @@ def random_operator(N, density, seed, hermitian=False, traceless=False):
     if traceless:
         X = X - np.trace(X) / N * np.eye(N)
     return CSR.from_dense(X)
+
+
+def random_banded(N, half_bandwidth, seed, hermitian=False, real=False):
+    """Seeded dense-band N x N operator: every entry with |col - row| <= half_bandwidth drawn
+    normal (complex unless ``real``); Hermitian by X + X^+ when asked."""
+    rng = np.random.default_rng(seed)
+    X = np.zeros((N, N), dtype=np.complex128)
+    rows, cols = np.nonzero(np.abs(np.subtract.outer(np.arange(N), np.arange(N))) <= half_bandwidth)
+    X[rows, cols] = rng.normal(size=rows.size)
+    if not real:
+        X[rows, cols] += 1j * rng.normal(size=rows.size)
+    if hermitian:
+        X = X + X.conj().T
+    return CSR.from_dense(X)
