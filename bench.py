@@ -89,7 +89,7 @@ class Clocks:
 
 def src_hash():
     h = hashlib.sha256()
-    for f in ("rk4.cu", "hyb.cu", "common.cuh"):
+    for f in ("rk4.cu", "stage.cuh", "hyb.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1812_11626_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -283,8 +283,8 @@ def main():
     traffic = None
     if os.path.exists(PROFILE_JSON):
         pj = json.load(open(PROFILE_JSON))
-        if pj.get("src_hash") == src_hash() and pj.get("variant") == variant:
-            traffic = pj.get("dram_bytes_per_launch")
+        if pj.get("src_hash") == src_hash():
+            traffic = pj.get("variants", {}).get(str(variant), {}).get("dram_bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch,
                 "kernel": kernel + " (fused SpMV + RK4 stage update, FP64)"}

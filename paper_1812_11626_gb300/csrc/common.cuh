@@ -135,6 +135,7 @@ struct MfBands {
     int bh = 0, bg = 0, bl = 0;   // half-bandwidths of the instantiation (H, Gamma, L)
     int P = 0;                    // channels
     bool real = false;            // every band real
+    bool h1_offdiag = false;      // H1 has entries off its diagonal (the FP32 stages load them)
     int n_tiles = 0, n_diag = 0;  // upper-triangle tiles, of which on the diagonal
     // FP64 stages: H0 + E H1 (+ sum theta_k H0_k), H1, Gamma = 1/2 sum gamma L^+L, L' = sqrt(gamma) L
     DBuf<double> h0, h1, g, l;

@@ -40,6 +40,7 @@
 // it needs (the rho' tile with its halo, the band coefficients of its rows and columns, and the
 // operands of its own stage updates), then evaluates X' from shared memory and applies the RK4
 // stage update to the two generators of every pair (j < k) and to the diagonal image (j = k).
+#include <algorithm>
 #include <cmath>
 #include <complex>
 
@@ -86,9 +87,10 @@ struct MfVec {
     T *gyn, *gacc;
 };
 
-__device__ inline long long pair_of(int N, int a, int b) {
-    return (long long)a * N - ((long long)a * (a + 1)) / 2 + (b - a - 1);
-}
+// lexicographic index of the pair a < b in 32-bit arithmetic (the matrix-free form keeps
+// N <= 32768, so D < 2^30)
+__device__ inline int pair_start(int N, int a) { return a * N - ((a * (a + 1)) >> 1) - a - 1; }
+__device__ inline int pair_of(int N, int a, int b) { return pair_start(N, a) + b; }
 
 // block-wide inclusive prefix sum of one value per thread; *total receives the block sum
 __device__ inline double block_incl_scan(double x, double *sh, double *total) {
@@ -154,37 +156,70 @@ __global__ void __launch_bounds__(kThreads) k_mf_post(int N, long long P2, const
     }
 }
 
-// rho' on a tile and its halo of BT rows and columns: all loads first, then the stores
+// rho' on a tile and its halo of BT rows and columns: all loads first, then the stores.  The
+// 32 central columns of every tile row go one per lane, with the pair index advancing by one
+// along the row; the 2 BT halo columns of all rows are a second, flat pass.
+template <int BT, typename T>
+__device__ inline typename Cx<T>::t rho_entry(const MfArgs &a, const MfVec<T> &q, int ai, int bi, int rowstart,
+                                              T diag0) {
+    typename Cx<T>::t val;
+    val.x = T(0);
+    val.y = T(0);
+    const int N = a.N;
+    if (ai >= 0 && ai < N && bi >= 0 && bi < N) {
+        if (ai < bi) {
+            const int p = rowstart + bi;
+            val.x = q.y[p];
+            val.y = -q.y[a.P2 + p];
+        } else if (ai > bi) {
+            const int p = pair_of(N, bi, ai);
+            val.x = q.y[p];
+            val.y = q.y[a.P2 + p];
+        } else {
+            val.x = diag0 + q.gi[ai];
+        }
+    }
+    return val;
+}
+
 template <int BT, typename T>
 __device__ inline void load_rho(typename Cx<T>::t *rho, const MfArgs &a, const MfVec<T> &q, int j0, int k0) {
     using C = typename Cx<T>::t;
-    constexpr int RW = kTK + 2 * BT, n = (kTJ + 2 * BT) * RW;
-    constexpr int IT = (n + kThreads - 1) / kThreads;
-    const int N = a.N;
-    const T diag0 = (T)(M_SQRT2 / (double)N);
-    C val[IT];
+    constexpr int RW = kTK + 2 * BT, RH = kTJ + 2 * BT;
+    constexpr int IT = (RH + kThreads / 32 - 1) / (kThreads / 32);     // central part, rows per warp
+    constexpr int nh = RH * 2 * BT, IH = (nh + kThreads - 1) / kThreads;  // halo columns
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const T diag0 = (T)(M_SQRT2 / (double)a.N);
+    C val[IT], hal[IH];
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        const int e = threadIdx.x + it * kThreads;
-        const int ra = e / RW, cb = e - ra * RW;
-        const int ai = j0 - BT + ra, bi = k0 - BT + cb;
+        const int ra = w + it * (kThreads / 32);
+        const int ai = j0 - BT + ra;
         val[it].x = T(0);
         val[it].y = T(0);
-        if (e < n && ai >= 0 && ai < N && bi >= 0 && bi < N) {
-            if (ai != bi) {
-                const bool up = ai < bi;
-                const long long p = up ? pair_of(N, ai, bi) : pair_of(N, bi, ai);
-                val[it].x = q.y[p];
-                val[it].y = up ? -q.y[a.P2 + p] : q.y[a.P2 + p];
-            } else {
-                val[it].x = diag0 + q.gi[ai];
-            }
-        }
+        if (ra < RH) val[it] = rho_entry<BT, T>(a, q, ai, k0 + lane, pair_start(a.N, ai), diag0);
+    }
+#pragma unroll
+    for (int it = 0; it < IH; ++it) {
+        const int e = threadIdx.x + it * kThreads;
+        const int ra = e / (2 * BT), h = e - ra * (2 * BT);
+        const int cb = h < BT ? h : kTK + h;       // columns [0, BT) and [BT + 32, RW)
+        const int ai = j0 - BT + ra;
+        hal[it].x = T(0);
+        hal[it].y = T(0);
+        if (e < nh) hal[it] = rho_entry<BT, T>(a, q, ai, k0 - BT + cb, pair_start(a.N, ai), diag0);
     }
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
+        const int ra = w + it * (kThreads / 32);
+        if (ra < RH) rho[ra * RW + BT + lane] = val[it];
+    }
+#pragma unroll
+    for (int it = 0; it < IH; ++it) {
         const int e = threadIdx.x + it * kThreads;
-        if (e < n) rho[e] = val[it];
+        const int ra = e / (2 * BT), h = e - ra * (2 * BT);
+        const int cb = h < BT ? h : kTK + h;
+        if (e < nh) rho[ra * RW + cb] = hal[it];
     }
 }
 
@@ -192,7 +227,7 @@ __device__ inline void load_rho(typename Cx<T>::t *rho, const MfArgs &a, const M
 // for j = k; operands loaded up front
 template <int STAGE, typename T>
 struct TileOut {
-    long long r[kRJ];     // pair index, or -2 - j for the diagonal j, or -1
+    int r[kRJ];           // pair index, or -2 - j for the diagonal j, or -1
     EpIn<T> s[kRJ], jv[kRJ];
     __device__ void prepare(const MfArgs &a, const MfVec<T> &q, int j0, int k0, int i0, int c) {
         const int k = k0 + c;
@@ -742,6 +777,7 @@ void build_fp32(MfBands &m, int N, int BH, int BL, int BR, int P, const std::vec
         split(H1(j, 0).real(), &dg[8 * (size_t)j + 2]);
         dg[8 * (size_t)j + 4] = off[j];
     }
+    m.h1_offdiag = std::any_of(h1o.begin(), h1o.end(), [](double x) { return x != 0.0; });
     upload(m.r32, r, s);
     upload(m.h1o32, h1o, s);
     upload(m.dg32, dg, s);
@@ -769,6 +805,7 @@ void mf_build(gksl_ctx *c, bool fp32) {
             bl = std::max(bl, half_bandwidth(c->diss[p]));
             real = real && op_real(c->diss[p]);
         }
+    GK_REQUIRE(N <= 32768, GKSL_ERR_ARG, "the matrix-free form is limited to N <= 32768");
     GK_REQUIRE(bh <= 4 && bl <= 4, GKSL_ERR_ARG,
                "the matrix-free form needs H0_k, H1 and L_p of half-bandwidth <= 4");
     const bool narrow = real && bh <= 1 && bl <= 1;
@@ -807,10 +844,11 @@ void mf_build(gksl_ctx *c, bool fp32) {
     upload(m.g, g, s);
     upload(m.l, l, s);
     if (fp32) build_fp32(m, N, BH, BL, narrow ? 2 : 8, (int)chans.size(), h0, h1, l, s);
-    const int nt = (N + kTJ - 1) / kTJ;
+    // every tile (rows [a TJ, (a+1) TJ), columns [b TK, (b+1) TK)) holding some j <= k
+    const int nt = (N + kTJ - 1) / kTJ, ntk = (N + kTK - 1) / kTK;
     std::vector<int> tiles;
     for (int a = 0; a < nt; ++a)
-        for (int b = a; b < nt; ++b) { tiles.push_back(a); tiles.push_back(b); }
+        for (int b = (a * kTJ) / kTK; b < ntk; ++b) { tiles.push_back(a); tiles.push_back(b); }
     m.tiles.alloc(tiles.size());
     GK_CUDA(cudaMemcpyAsync(m.tiles.p, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, s));
     m.n_tiles = (int)(tiles.size() / 2);
@@ -870,7 +908,7 @@ void mf_step(gksl_ctx *c, int precision, double h, const double *tab, long long 
         if (narrow) Narrow64::step(a, op, grid, c->stream, c);
         else Wide64::step(a, op, grid, c->stream, c);
     } else {
-        MfOps32 op{m.r32.p, m.h1o32.p, m.dg32.p, m.lo32.p, m.ld32.p};
+        MfOps32 op{m.r32.p, m.h1_offdiag ? m.h1o32.p : nullptr, m.dg32.p, m.lo32.p, m.ld32.p};
         if (narrow) Narrow32::step(a, op, grid, c->stream, c);
         else Wide32::step(a, op, grid, c->stream, c);
     }
