@@ -14,8 +14,14 @@
 // products u_c . Y_i.  Each stage is one fused kernel; gradient partial sums are kept per
 // block in fixed slots and reduced in a fixed order at the end (deterministic).
 //
-// Memory: period checkpoints, then per period sqrt(S)-spaced checkpoints, then the states of
-// one segment; each state is recomputed at most twice.
+// Schedule: period checkpoints from one forward pass; then, period by period in reverse,
+// checkpoints every q steps (q ~ sqrt(S/4)), and segment by segment in reverse one CUDA graph
+// that re-runs the segment's q steps forward, keeping every stage input Y1..Y4 of each step,
+// and then sweeps the same steps backwards.  Every per-step scalar (the drive at the stage
+// times, the loss weight of the step) is read from device tables indexed by the step, so one
+// graph per segment length serves every segment.  Each state is recomputed at most twice;
+// memory is (periods + S/q) state checkpoints plus 4 q stage inputs.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -29,128 +35,301 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxCh = gksl_ctx::kMaxCh;
-constexpr int kMaxPar = kMaxCh;
 
 template <typename VT>
 struct AdjArgs {
     HybView<VT> ch[kMaxCh];
     double chw[kMaxCh];     // weight of channel c in A^T
-    int gidx[kMaxCh];       // gradient slot of channel c
-    double gfac[kMaxCh];    // factor of u_c . Y in that slot (sin(omega t) for the drive amplitude)
     int nch;
     const double *kp[GKSL_MAX_P];   // K_p per unit rate: d b / d gamma_p
-    int kp_gidx[GKSL_MAX_P];
     int nkp;
-    int npar;
-    double alpha;   // kb = alpha * x
+    int q1ch;                  // channel of Q1 (-1: none): weight E + A theta, gradient factor theta
+    double E, A;
+    const double *theta;       // theta(t) at the three stage times of every step
+    const long long *base;     // the step is *base + local
+    long long local;
+    long long first, S;        // loss period: steps [first, first + S)
+    double w_edge, w_mid;      // trapezoid weights 1/(2S) and 1/S (stage 1: lam += weight * w)
     double h, h2, h3, h6;   // h, h/2, h/3, h/6 (computed on the host)
-    double beta;    // stage 1: lam += beta * w
     const int *long_rows;
     long long n_long;
     int nb_long;
     long long D;
 };
 
+// (C x)_r over the ELL slots of row r; the slot loads go out four at a time before their gathers
 template <typename VT>
 __device__ inline double ell_row(const HybView<VT> &H, long long r, const VT *__restrict__ x) {
     double s = 0.0;
-    for (int j = 0; j < H.width; ++j) {
+    const int wd = H.width;
+    int j = 0;
+    for (; j + 4 <= wd; j += 4) {
+        int cc[4];
+        VT vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            long long p = (long long)(j + u) * H.ld + r;
+            cc[u] = __ldcs(H.ell_col + p);
+            vv[u] = __ldcs(H.ell_val + p);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s += (double)vv[u] * (double)__ldg(x + cc[u]);
+    }
+    for (; j < wd; ++j) {
         long long p = (long long)j * H.ld + r;
         s += (double)__ldcs(H.ell_val + p) * (double)__ldg(x + __ldcs(H.ell_col + p));
     }
     return s;
 }
 
+// (C x)_r of a long row by one warp: four entries per lane in flight, then a warp reduction
 template <typename VT>
 __device__ inline double tail_row(const HybView<VT> &H, long long i, int lane, const VT *__restrict__ x) {
     double s = 0.0;
-    for (int e = H.tail_ptr[i] + lane; e < H.tail_ptr[i + 1]; e += 32)
-        s += (double)__ldcs(H.tail_val + e) * (double)__ldg(x + H.tail_col[e]);
+    const int e1 = H.tail_ptr[i + 1];
+    int e = H.tail_ptr[i] + lane;
+    for (; e + 96 < e1; e += 128) {
+        int cc[4];
+        VT vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            cc[u] = H.tail_col[e + 32 * u];
+            vv[u] = __ldcs(H.tail_val + e + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s += (double)vv[u] * (double)__ldg(x + cc[u]);
+    }
+    for (; e < e1; e += 32) s += (double)__ldcs(H.tail_val + e) * (double)__ldg(x + H.tail_col[e]);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
+}
+
+// Warp sums of the 8 values v[0..7] of every lane in 9 shuffle-adds: each round halves the set
+// a lane keeps (bits 16, 8, 4 of the lane index pick the half), the last two rounds finish the
+// sum inside groups of four lanes.  Afterwards lane l holds the sum of slot
+// 4 (l >> 4 & 1) + 2 (l >> 3 & 1) + (l >> 2 & 1) in v[0].
+__device__ inline void warp_sum8(double v[8], int lane) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool hi = lane & 16;
+        const double send = hi ? v[k] : v[k + 4];
+        const double keep = hi ? v[k + 4] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool hi = lane & 8;
+        const double send = hi ? v[k] : v[k + 2];
+        const double keep = hi ? v[k + 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const bool hi = lane & 4;
+        const double send = hi ? v[0] : v[1];
+        const double keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 template <int STAGE, typename VT>
 __device__ inline void adj_epilogue(const AdjArgs<VT> &a, long long r, double ybar, const double *__restrict__ lam,
                                     double *__restrict__ lacc, VT *__restrict__ kb_out, const double *__restrict__ w,
-                                    double *lam_out) {
+                                    double *lam_out, double beta) {
     if (STAGE == 4) { kb_out[r] = (VT)(a.h3 * lam[r] + a.h * ybar); lacc[r] = lam[r] + ybar; }
     if (STAGE == 3) { kb_out[r] = (VT)(a.h3 * lam[r] + a.h2 * ybar); lacc[r] = lacc[r] + ybar; }
     if (STAGE == 2) { kb_out[r] = (VT)(a.h6 * lam[r] + a.h2 * ybar); lacc[r] = lacc[r] + ybar; }
-    if (STAGE == 1) { lam_out[r] = lacc[r] + ybar + a.beta * w[r]; }
+    if (STAGE == 1) { lam_out[r] = lacc[r] + ybar + beta * w[r]; }
 }
 
-// x: gathered vector (lam' for stage 4, kb_i otherwise); Y: forward stage input Y_i (own row)
-template <int STAGE, typename VT>
+// One reverse stage for NC >= nch channels.  x: the gathered vector (lam' for stage 4, kb_i
+// otherwise); Y: the forward stage input Y_i (own row).  Threads walk rows with a grid stride
+// (the first nb_long blocks: one warp per long row; the rest: one thread per ELL row) and keep
+// their gradient partials in registers: slot c collects u_c . Y (u_c = (C_c x)_r), slot NC + q
+// collects x . K_q.  The constant factors of a launch (alpha = h/6 at stage 4, theta(t) of the
+// Q1 slot) are applied once per block when the partials go to this block's fixed slots of
+// `part`; the host maps slots to parameters.
+template <int STAGE, typename VT, int NC>
 __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *__restrict__ x,
                                                      const VT *__restrict__ Y, const double *lam, double *lacc,
                                                      VT *__restrict__ kb_out, const double *__restrict__ w,
                                                      double *lam_out, double *__restrict__ part) {
-    double g[kMaxPar];
+    constexpr int NSLOT = 2 * NC;
+    const long long step = *a.base + a.local;
+    const double th = a.theta[3 * step + (STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1))];
+    const double alpha = STAGE == 4 ? a.h6 : 1.0;   // kb = alpha * x
+    double beta = 0.0;
+    if (STAGE == 1) {
+        const long long m = step - a.first;
+        beta = (m >= 0 && m < a.S) ? (m == 0 ? a.w_edge : a.w_mid) : 0.0;
+    }
+    double chw[NC];
 #pragma unroll
-    for (int k = 0; k < kMaxPar; ++k) g[k] = 0.0;
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    bool active = false;
-    long long r = -1;
-    double u[kMaxCh];
+    for (int c = 0; c < NC; ++c) chw[c] = c == a.q1ch ? a.E + a.A * th : (c < a.nch ? a.chw[c] : 0.0);
+    double g[NSLOT];
+#pragma unroll
+    for (int k = 0; k < NSLOT; ++k) g[k] = 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double u[NC];
+    // own-row part of the stage: the epilogue and the gradient partials of row r
+    auto finish_row = [&](long long r, const double (&u)[NC]) {
+        const double yr = (double)Y[r];
+        double ysum = 0.0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (c < a.nch) {
+                ysum += chw[c] * u[c];
+                g[c] += u[c] * yr;
+            }
+        const double xr = (double)x[r];
+#pragma unroll
+        for (int q = 0; q < NC; ++q)
+            if (q < a.nkp) g[NC + q] += xr * a.kp[q][r];
+        adj_epilogue<STAGE, VT>(a, r, alpha * ysum, lam, lacc, kb_out, w, lam_out, beta);
+    };
     if ((int)blockIdx.x < a.nb_long) {
-        long long i = (long long)blockIdx.x * kWarps + warp;
-        if (i < a.n_long) {
-            r = a.long_rows[i];
+        for (long long i = (long long)blockIdx.x * kWarps + warp; i < a.n_long; i += (long long)a.nb_long * kWarps) {
 #pragma unroll
-            for (int c = 0; c < kMaxCh; ++c)
-                if (c < a.nch) u[c] = tail_row<VT>(a.ch[c], i, lane, x);
-            active = lane == 0;
+            for (int c = 0; c < NC; ++c) u[c] = c < a.nch ? tail_row<VT>(a.ch[c], i, lane, x) : 0.0;
+            if (lane == 0) finish_row(a.long_rows[i], u);
         }
     } else {
-        r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
-        if (r < a.D && __ldcs(a.ch[0].ell_col + r) >= 0) {
+        const long long stride = (long long)(gridDim.x - a.nb_long) * kThreads;
+        for (long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x; r < a.D; r += stride) {
+            if (__ldcs(a.ch[0].ell_col + r) < 0) continue;   // long row, handled by a warp above
 #pragma unroll
-            for (int c = 0; c < kMaxCh; ++c)
-                if (c < a.nch) u[c] = ell_row<VT>(a.ch[c], r, x);
-            active = true;
+            for (int c = 0; c < NC; ++c) u[c] = c < a.nch ? ell_row<VT>(a.ch[c], r, x) : 0.0;
+            finish_row(r, u);
         }
     }
-    if (active) {
-        double ybar = 0.0;
-        double yr = (double)Y[r];
+    // block reduction of the partials into this block's fixed slots
+    __shared__ double red[kWarps][NSLOT];
+    if constexpr (NSLOT == 8) {
+        warp_sum8(g, lane);
+        if ((lane & 3) == 0) red[warp][4 * (lane >> 4 & 1) + 2 * (lane >> 3 & 1) + (lane >> 2 & 1)] = g[0];
+    } else {
 #pragma unroll
-        for (int c = 0; c < kMaxCh; ++c)
-            if (c < a.nch) {
-                double uc = a.alpha * u[c];
-                ybar += a.chw[c] * uc;
-#pragma unroll
-                for (int k = 0; k < kMaxPar; ++k)
-                    if (k == a.gidx[c]) g[k] += a.gfac[c] * uc * yr;
-            }
-        double xr = a.alpha * (double)x[r];
-        for (int q = 0; q < a.nkp; ++q) {
-            double kv = a.kp[q][r];
-#pragma unroll
-            for (int k = 0; k < kMaxPar; ++k)
-                if (k == a.kp_gidx[q]) g[k] += xr * kv;
+        for (int k = 0; k < NSLOT; ++k) {
+            double v = g[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
         }
-        adj_epilogue<STAGE, VT>(a, r, ybar, lam, lacc, kb_out, w, lam_out);
-    }
-    // block reduction of the gradient partials into this block's fixed slots
-    __shared__ double red[kWarps][kMaxPar];
-#pragma unroll
-    for (int k = 0; k < kMaxPar; ++k) {
-        double v = g[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < a.npar) {
-        double s = 0.0;
-        for (int ww = 0; ww < kWarps; ++ww) s += red[ww][threadIdx.x];
-        part[(long long)blockIdx.x * a.npar + threadIdx.x] += s;
+    if (threadIdx.x < NSLOT) {
+        const int k = threadIdx.x;
+        double sum = 0.0;
+        for (int ww = 0; ww < kWarps; ++ww) sum += red[ww][k];
+        double f = alpha;
+        if (k == a.q1ch) f *= th;
+        part[(long long)blockIdx.x * NSLOT + k] += f * sum;
     }
+}
+
+// blocks of one reverse stage: up to one per SM for the long rows (a warp each), then the ELL
+// rows (a thread each), both walked with a grid stride; at most four blocks per SM in all (the
+// register budget of the 4-channel kernel), so the whole grid is resident at once
+struct AdjGrid {
+    int nb_long;
+    unsigned total;
+};
+
+AdjGrid adj_grid(long long n_long, long long D, int sms) {
+    long long nl = std::min<long long>((n_long + kWarps - 1) / kWarps, sms);
+    long long ne = std::min<long long>((D + kThreads - 1) / kThreads, 4LL * sms - nl);
+    return AdjGrid{(int)nl, (unsigned)(nl + std::max(1LL, ne))};
 }
 
 __global__ void k_fill_scaled(double *__restrict__ y, const double *__restrict__ x, double a, long long n) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = a * x[i];
+}
+
+__global__ void k_fill1(void *p, long long n, int fp32) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (fp32) ((float *)p)[i] = 1.0f;
+    else ((double *)p)[i] = 1.0;
+}
+
+// <O> = c0 + sum_l w_l v_{D^l} of the state at grid point m = *base + local - first of the
+// loss period (nothing outside it); one block, fixed-order reduction
+__global__ void k_obs_step(const double *__restrict__ w, const double *__restrict__ c0, long long P2, int N,
+                           const double *__restrict__ v, const long long *base, long long local, long long first,
+                           long long S, double *__restrict__ out) {
+    const long long m = *base + local - first;
+    if (m < 0 || m > S) return;
+    double s = 0.0;
+    for (int l = threadIdx.x; l < N - 1; l += blockDim.x) s += w[2 * P2 + l] * v[2 * P2 + l];
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[m] = *c0 + red[0];
+}
+
+// a stream capture that is ended (and its graph dropped) if the capturing code throws
+struct Capture {
+    cudaStream_t s;
+    bool open = false;
+    explicit Capture(cudaStream_t st) : s(st) {
+        GK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        open = true;
+    }
+    cudaGraphExec_t finish() {
+        cudaGraph_t g;
+        open = false;
+        GK_CUDA(cudaStreamEndCapture(s, &g));
+        cudaGraphExec_t e;
+        cudaError_t err = cudaGraphInstantiate(&e, g, 0);
+        cudaGraphDestroy(g);
+        GK_CUDA(err);
+        return e;
+    }
+    ~Capture() {
+        if (open) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+        }
+    }
+};
+
+struct ExecSet {
+    struct E {
+        long long len;
+        int mode;
+        cudaGraphExec_t exec;
+    };
+    std::vector<E> v;
+    ~ExecSet() {
+        for (auto &e : v) cudaGraphExecDestroy(e.exec);
+    }
+};
+
+// the four reverse stages of one step: kb4 from lam', then kb3, kb2, and lam from kb1
+template <typename VT, int NC>
+void rev_stages_t(const AdjArgs<VT> &a, unsigned grid, cudaStream_t s, const VT *lam_in, const VT *Y1, const VT *Y2,
+                  const VT *Y3, const VT *Y4, VT *ka, VT *kb, double *lam, double *lacc, const double *w,
+                  double *part) {
+    k_adjoint<4, VT, NC><<<grid, kThreads, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
+    k_adjoint<3, VT, NC><<<grid, kThreads, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
+    k_adjoint<2, VT, NC><<<grid, kThreads, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
+    k_adjoint<1, VT, NC><<<grid, kThreads, 0, s>>>(a, ka, Y1, lam, lacc, nullptr, w, lam, part);
+}
+
+// the four reverse stages of one step: kb4 from lam', then kb3, kb2, and lam from kb1
+template <typename VT>
+void rev_stages(const AdjArgs<VT> &a, int NC, unsigned grid, cudaStream_t s, const VT *lam_in, const VT *Y1,
+                const VT *Y2, const VT *Y3, const VT *Y4, VT *ka, VT *kb, double *lam, double *lacc, const double *w,
+                double *part) {
+    if (NC == 4) rev_stages_t<VT, 4>(a, grid, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part);
+    else rev_stages_t<VT, kMaxCh>(a, grid, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part);
 }
 
 }  // namespace
@@ -165,6 +344,7 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
         GK_REQUIRE(c->asm_flags & GKSL_ASM_FP32, GKSL_ERR_STATE, "precision 32 needs gksl_assemble with GKSL_ASM_FP32");
     cudaStream_t s = c->stream;
     const long long D = c->D, D1 = D + 1;
+    const bool f32 = precision == 32;
     // parameter layout [A, gamma_p..., theta_k...]
     int nP = 0, nK = 0;
     for (int p = 0; p < GKSL_MAX_P; ++p) nP += c->has_r[p];
@@ -172,13 +352,15 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
     const int npar = 1 + nP + nK;
     GK_REQUIRE(n_grad == npar, GKSL_ERR_ARG,
                "n_grad must equal 1 + (number of dissipators) + (number of H0 components) = " + std::to_string(npar));
-    ensure_work(c, precision == 32);
+    ensure_work(c, f32);
     const double T = 2.0 * M_PI / c->omega;
     const double h = T / (double)S;
     const long long nsteps = period * S, first = (period - 1) * S;
     const double t0 = c->t;
     check_drive_grid(c, S, h);
     fill_eps_table(c, t0, h, nsteps);
+    DBuf<double> theta((size_t)(3 * nsteps));
+    fill_theta_table(c, t0, h, nsteps, theta.p);
 
     // channel descriptors
     int slot_gamma[GKSL_MAX_P], slot_theta[GKSL_MAX_H0];
@@ -189,185 +371,171 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
     }
     AdjArgs<double> a64{};
     AdjArgs<float> a32{};
+    // gradient slot of each channel and of each K_p (the kernel's partials are per channel)
+    int gidx[kMaxCh], kp_gidx[GKSL_MAX_P];
     auto setup = [&](auto &a, auto view_of) {
         a.nch = c->adj_n;
-        a.npar = npar;
+        a.q1ch = -1;
         for (int i = 0; i < c->adj_n; ++i) {
             a.ch[i] = view_of(i);
             int kind = c->adj_kind[i], idx = c->adj_index[i];
-            if (kind == 0) { a.chw[i] = c->h0[idx].weight; a.gidx[i] = slot_theta[idx]; a.gfac[i] = 1.0; }
-            if (kind == 1) { a.chw[i] = 0.0; a.gidx[i] = 0; a.gfac[i] = 0.0; }   // set per stage
-            if (kind == 2) { a.chw[i] = c->diss[idx].weight; a.gidx[i] = slot_gamma[idx]; a.gfac[i] = 1.0; }
+            if (kind == 0) { a.chw[i] = c->h0[idx].weight; gidx[i] = slot_theta[idx]; }
+            if (kind == 1) { a.chw[i] = 0.0; gidx[i] = 0; a.q1ch = i; }   // E + A theta(t), on the device
+            if (kind == 2) { a.chw[i] = c->diss[idx].weight; gidx[i] = slot_gamma[idx]; }
         }
         a.nkp = 0;
         for (int p = 0; p < GKSL_MAX_P; ++p)
-            if (c->has_r[p]) { a.kp[a.nkp] = c->Kp[p].p; a.kp_gidx[a.nkp++] = slot_gamma[p]; }
+            if (c->has_r[p]) { a.kp[a.nkp] = c->Kp[p].p; kp_gidx[a.nkp++] = slot_gamma[p]; }
+        a.E = c->E;
+        a.A = c->A;
+        a.theta = theta.p;
+        a.base = c->step_base.p;
+        a.first = first;
+        a.S = S;
+        a.w_edge = 0.5 / (double)S;
+        a.w_mid = 1.0 / (double)S;
         a.h = h;
         a.h2 = 0.5 * h;
         a.h3 = h / 3.0;
         a.h6 = h / 6.0;
         a.long_rows = c->adj[0].long_rows.p;
         a.n_long = c->adj[0].n_long;
-        a.nb_long = (int)((a.n_long + kWarps - 1) / kWarps);
         a.D = D;
     };
     setup(a64, [&](int i) { return view(c->adj[i]); });
-    if (precision == 32) setup(a32, [&](int i) { return view(c->adjf[i]); });
-    int q1ch = -1;
-    for (int i = 0; i < c->adj_n; ++i)
-        if (c->adj_kind[i] == 1) q1ch = i;
-    const unsigned grid = (unsigned)(a64.nb_long + (D + kThreads - 1) / kThreads);
+    if (f32) setup(a32, [&](int i) { return view(c->adjf[i]); });
+    int sms = 0;
+    GK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const AdjGrid ag = adj_grid(a64.n_long, D, sms);
+    a64.nb_long = a32.nb_long = ag.nb_long;
+    const unsigned grid = ag.total;
+    // channels compiled into the kernel: 4 (one dissipator, up to two H0 components), or all
+    const int NC = c->adj_n <= 4 ? 4 : kMaxCh;
+    const int nslot = 2 * NC;
 
     // observable weights (dense, zero off the D block)
     DBuf<double> w((size_t)D1), c0(1);
     GK_CUDA(cudaMemsetAsync(w.p, 0, sizeof(double) * D1, s));
     observable_weights(c, o_diag, w.p, c0.p);
-    // trapezoid weights of the loss period
-    std::vector<double> wt((size_t)S + 1, 1.0 / (double)S);
-    wt[0] = wt[S] = 0.5 / (double)S;
+    const Basis B(c->N);
 
-    // buffers
-    DBuf<double> v_save((size_t)D1), ckP((size_t)(period * D1));
-    const long long q = std::max(1LL, (long long)std::ceil(std::sqrt((double)S)));
+    // checkpoints: one per period, one every q steps of the period being reversed
+    const long long q = std::max(1LL, std::min(S, (long long)std::ceil(std::sqrt((double)S / 4.0))));
     const long long nseg = (S + q - 1) / q;
-    DBuf<double> seg((size_t)(nseg * D1)), traj((size_t)((q + 1) * D1));
+    DBuf<double> v_save((size_t)D1), ckP((size_t)(period * D1)), seg((size_t)(nseg * D1));
     DBuf<double> lam((size_t)D1), lacc((size_t)D1), obs((size_t)(S + 1));
-    DBuf<double> part((size_t)grid * npar);
-    GK_CUDA(cudaMemsetAsync(part.p, 0, sizeof(double) * grid * npar, s));
-    // stage inputs and adjoint vectors in the working precision
-    DBuf<double> Y2d, Y3d, Y4d, kbAd, kbBd;
-    DBuf<float> Y1f, Y2f, Y3f, Y4f, kbAf, kbBf, lamf;
-    // stage inputs carry the constant 1 at index D (it multiplies the K column)
-    const double one = 1.0;
-    const float onef = 1.0f;
-    if (precision == 64) {
-        Y2d.alloc((size_t)D1); Y3d.alloc((size_t)D1); Y4d.alloc((size_t)D1);
-        kbAd.alloc((size_t)D1); kbBd.alloc((size_t)D1);
-        for (double *p : {Y2d.p, Y3d.p, Y4d.p})
-            GK_CUDA(cudaMemcpyAsync(p + D, &one, sizeof(double), cudaMemcpyHostToDevice, s));
-    } else {
-        Y1f.alloc((size_t)D1); Y2f.alloc((size_t)D1); Y3f.alloc((size_t)D1); Y4f.alloc((size_t)D1);
-        kbAf.alloc((size_t)D1); kbBf.alloc((size_t)D1); lamf.alloc((size_t)D1);
-        for (float *p : {Y1f.p, Y2f.p, Y3f.p, Y4f.p})
-            GK_CUDA(cudaMemcpyAsync(p + D, &onef, sizeof(float), cudaMemcpyHostToDevice, s));
-    }
-    GK_CUDA(cudaStreamSynchronize(s));
+    DBuf<double> part((size_t)grid * nslot);
+    GK_CUDA(cudaMemsetAsync(part.p, 0, sizeof(double) * grid * nslot, s));
+    // stage inputs Y1..Y4 of the q steps of one segment, in the working precision; each vector
+    // carries the constant 1 at index D (it multiplies the K column)
+    const size_t esz = f32 ? sizeof(float) : sizeof(double);
+    const long long ytot = 4 * q * D1;
+    DBuf<char> ybuf((size_t)ytot * esz), kbA((size_t)D1 * esz), kbB((size_t)D1 * esz);
+    DBuf<float> lamf;
+    if (f32) lamf.alloc((size_t)D1);
+    k_fill1<<<grid_for(ytot, 256), 256, 0, s>>>(ybuf.p, ytot, f32 ? 1 : 0);
+    GK_LAUNCH_CHECK();
+    auto Yp = [&](int k, long long i) -> void * { return ybuf.p + (size_t)((k * q + i) * D1) * esz; };
     GK_CUDA(cudaMemcpyAsync(v_save.p, c->v.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, s));
 
     auto load_state = [&](const double *src) {
         GK_CUDA(cudaMemcpyAsync(c->v.p, src, sizeof(double) * D1, cudaMemcpyDeviceToDevice, s));
-        if (precision == 32) to_f32(c->v.p, c->v32.p, D1, s);
+        if (f32) to_f32(c->v.p, c->v32.p, D1, s);
     };
     auto save_state = [&](double *dst) {
         GK_CUDA(cudaMemcpyAsync(dst, c->v.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, s));
     };
 
-    // 1. forward pass: period checkpoints
+    // one reverse step (the four adjoint stages) of local step i of a segment
+    auto reverse_step = [&](long long i) {
+        if (f32) {
+            to_f32(lam.p, lamf.p, D1, s);
+            AdjArgs<float> a = a32;
+            a.local = i;
+            const float *Y1 = (const float *)Yp(0, i), *Y2 = (const float *)Yp(1, i), *Y3 = (const float *)Yp(2, i),
+                        *Y4 = (const float *)Yp(3, i);
+            float *ka = (float *)kbA.p, *kb = (float *)kbB.p;
+            rev_stages<float>(a, NC, grid, s, lamf.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p, part.p);
+        } else {
+            AdjArgs<double> a = a64;
+            a.local = i;
+            const double *Y1 = (const double *)Yp(0, i), *Y2 = (const double *)Yp(1, i),
+                         *Y3 = (const double *)Yp(2, i), *Y4 = (const double *)Yp(3, i);
+            double *ka = (double *)kbA.p, *kb = (double *)kbB.p;
+            rev_stages<double>(a, NC, grid, s, lam.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p, part.p);
+        }
+        GK_LAUNCH_CHECK();
+    };
+    auto obs_node = [&](long long local) {
+        k_obs_step<<<1, 256, 0, s>>>(w.p, c0.p, B.P2, c->N, c->v.p, c->step_base.p, local, first, S, obs.p);
+        GK_LAUNCH_CHECK();
+    };
+    // graph of one segment of len steps from the context state at step *step_base:
+    // mode 0: forward only; mode 1: forward keeping Y1..Y4, then the reverse sweep; mode 2: as 1
+    // with the observable at every grid point (the loss period)
+    ExecSet execs;
+    auto segment_graph = [&](long long len, int mode) -> cudaGraphExec_t {
+        for (auto &e : execs.v)
+            if (e.len == len && e.mode == mode) return e.exec;
+        Capture cap(s);
+        for (long long i = 0; i < len; ++i) {
+            if (mode > 0) {
+                if (f32) GK_CUDA(cudaMemcpyAsync(Yp(0, i), c->v32.p, sizeof(float) * D1, cudaMemcpyDeviceToDevice, s));
+                else GK_CUDA(cudaMemcpyAsync(Yp(0, i), c->v.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, s));
+            }
+            if (mode == 2) obs_node(i);
+            if (mode > 0) step_into(c, precision, h, i, Yp(1, i), Yp(2, i), Yp(3, i));
+            else step_into(c, precision, h, i, nullptr, nullptr, nullptr);
+        }
+        if (mode == 2) obs_node(len);
+        if (mode > 0)
+            for (long long i = len - 1; i >= 0; --i) reverse_step(i);
+        cudaGraphExec_t e = cap.finish();
+        execs.v.push_back({len, mode, e});
+        return e;
+    };
+
+    // 1. forward pass: period checkpoints (the last period's end state is not needed)
     load_state(v_save.p);
     for (long long p = 0; p < period; ++p) {
         save_state(ckP.p + p * D1);
-        advance(c, precision, h, p * S, S);
+        if (p + 1 < period) advance(c, precision, h, p * S, S);
     }
-    // 2. reverse sweep
-    k_fill_scaled<<<grid_for(D1, 256), 256, 0, s>>>(lam.p, w.p, wt[S], D1);
+    // 2. reverse sweep; lam starts as dL/dv at the last grid point
+    k_fill_scaled<<<grid_for(D1, 256), 256, 0, s>>>(lam.p, w.p, 0.5 / (double)S, D1);
     GK_LAUNCH_CHECK();
     for (long long p = period - 1; p >= 0; --p) {
-        // sqrt(S)-spaced checkpoints of this period (and the observable on the loss period)
         load_state(ckP.p + p * D1);
-        const bool loss_period = (p == period - 1);
+        const int mode = (p == period - 1) ? 2 : 1;
         for (long long j = 0; j < nseg; ++j) {
             save_state(seg.p + j * D1);
-            long long len = std::min(q, S - j * q);
-            if (loss_period) {
-                for (long long i = 0; i < len; ++i) {
-                    observable_apply(c, w.p, c0.p, c->v.p, 1, D1, obs.p + j * q + i);
-                    advance(c, precision, h, p * S + j * q + i, 1);
-                }
-            } else {
-                advance(c, precision, h, p * S + j * q, len);
-            }
+            if (j + 1 == nseg) break;   // the last segment starts from this checkpoint
+            set_step_base(c, p * S + j * q);
+            GK_CUDA(cudaGraphLaunch(segment_graph(q, 0), s));
         }
-        if (loss_period) observable_apply(c, w.p, c0.p, c->v.p, 1, D1, obs.p + S);
         for (long long j = nseg - 1; j >= 0; --j) {
-            long long len = std::min(q, S - j * q);
+            const long long len = std::min(q, S - j * q);
             load_state(seg.p + j * D1);
-            save_state(traj.p);
-            for (long long i = 0; i < len; ++i) {
-                advance(c, precision, h, p * S + j * q + i, 1);
-                save_state(traj.p + (i + 1) * D1);
-            }
-            for (long long i = len - 1; i >= 0; --i) {
-                const long long gstep = p * S + j * q + i;
-                const double tn = t0 + (double)gstep * h;
-                double th3[3];
-                drive_theta(c->drive_shape, c->omega, tn, h, th3);
-                const double thst[4] = {th3[0], th3[1], th3[1], th3[2]};   // theta at stages 1..4
-                const long long m = gstep - first;
-                const double beta = (m >= 0 && m < S) ? wt[m] : 0.0;
-                double *vn = traj.p + i * D1;
-                if (precision == 64) {
-                    forward_stage_inputs(c, 64, h, gstep, vn, Y2d.p, Y3d.p, Y4d.p);
-                    const double *Ys[4] = {vn, Y2d.p, Y3d.p, Y4d.p};
-                    for (int st = 4; st >= 1; --st) {
-                        double sn = thst[st - 1];
-                        if (q1ch >= 0) {
-                            a64.chw[q1ch] = c->E + c->A * sn;
-                            a64.gfac[q1ch] = sn;
-                        }
-                        a64.alpha = st == 4 ? h / 6.0 : 1.0;
-                        a64.beta = beta;
-                        const double *xin = st == 4 ? lam.p : (st == 3 ? kbAd.p : (st == 2 ? kbBd.p : kbAd.p));
-                        double *kout = st == 4 ? kbAd.p : (st == 3 ? kbBd.p : (st == 2 ? kbAd.p : nullptr));
-                        const double *Y = Ys[st - 1];
-                        switch (st) {
-                            case 4: k_adjoint<4, double><<<grid, kThreads, 0, s>>>(a64, xin, Y, lam.p, lacc.p, kout, w.p, lam.p, part.p); break;
-                            case 3: k_adjoint<3, double><<<grid, kThreads, 0, s>>>(a64, xin, Y, lam.p, lacc.p, kout, w.p, lam.p, part.p); break;
-                            case 2: k_adjoint<2, double><<<grid, kThreads, 0, s>>>(a64, xin, Y, lam.p, lacc.p, kout, w.p, lam.p, part.p); break;
-                            case 1: k_adjoint<1, double><<<grid, kThreads, 0, s>>>(a64, xin, Y, lam.p, lacc.p, kout, w.p, lam.p, part.p); break;
-                        }
-                        GK_LAUNCH_CHECK();
-                    }
-                } else {
-                    to_f32(vn, Y1f.p, D1, s);
-                    forward_stage_inputs(c, 32, h, gstep, Y1f.p, Y2f.p, Y3f.p, Y4f.p);
-                    to_f32(lam.p, lamf.p, D1, s);
-                    const float *Ys[4] = {Y1f.p, Y2f.p, Y3f.p, Y4f.p};
-                    for (int st = 4; st >= 1; --st) {
-                        double sn = thst[st - 1];
-                        if (q1ch >= 0) {
-                            a32.chw[q1ch] = c->E + c->A * sn;
-                            a32.gfac[q1ch] = sn;
-                        }
-                        a32.alpha = st == 4 ? h / 6.0 : 1.0;
-                        a32.beta = beta;
-                        const float *xin = st == 4 ? lamf.p : (st == 3 ? kbAf.p : (st == 2 ? kbBf.p : kbAf.p));
-                        float *kout = st == 4 ? kbAf.p : (st == 3 ? kbBf.p : (st == 2 ? kbAf.p : nullptr));
-                        const float *Y = Ys[st - 1];
-                        switch (st) {
-                            case 4: k_adjoint<4, float><<<grid, kThreads, 0, s>>>(a32, xin, Y, lam.p, lacc.p, kout, w.p, lam.p, part.p); break;
-                            case 3: k_adjoint<3, float><<<grid, kThreads, 0, s>>>(a32, xin, Y, lam.p, lacc.p, kout, w.p, lam.p, part.p); break;
-                            case 2: k_adjoint<2, float><<<grid, kThreads, 0, s>>>(a32, xin, Y, lam.p, lacc.p, kout, w.p, lam.p, part.p); break;
-                            case 1: k_adjoint<1, float><<<grid, kThreads, 0, s>>>(a32, xin, Y, lam.p, lacc.p, kout, w.p, lam.p, part.p); break;
-                        }
-                        GK_LAUNCH_CHECK();
-                    }
-                }
-            }
+            set_step_base(c, p * S + j * q);
+            GK_CUDA(cudaGraphLaunch(segment_graph(len, mode), s));
         }
     }
     // 3. loss and gradient, reduced in a fixed order
-    std::vector<double> ho((size_t)S + 1), hp((size_t)grid * npar);
+    std::vector<double> ho((size_t)S + 1), hp((size_t)grid * nslot);
     GK_CUDA(cudaMemcpyAsync(ho.data(), obs.p, sizeof(double) * (S + 1), cudaMemcpyDeviceToHost, s));
-    GK_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * grid * npar, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * grid * nslot, cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
     double L = 0.0;
-    for (long long m = 0; m <= S; ++m) L += wt[m] * ho[m];
+    for (long long m = 0; m <= S; ++m) L += (m == 0 || m == S ? 0.5 / (double)S : 1.0 / (double)S) * ho[m];
     *loss = L;
-    for (int k = 0; k < npar; ++k) {
+    auto slot_sum = [&](int k) {
         double g = 0.0;
-        for (unsigned b = 0; b < grid; ++b) g += hp[(size_t)b * npar + k];
-        grad[k] = g;
-    }
+        for (unsigned b = 0; b < grid; ++b) g += hp[(size_t)b * nslot + k];
+        return g;
+    };
+    for (int k = 0; k < npar; ++k) grad[k] = 0.0;
+    for (int i = 0; i < c->adj_n; ++i) grad[gidx[i]] += slot_sum(i);
+    for (int q = 0; q < a64.nkp; ++q) grad[kp_gidx[q]] += slot_sum(NC + q);
     // restore the state
     load_state(v_save.p);
     GK_CUDA(cudaStreamSynchronize(s));

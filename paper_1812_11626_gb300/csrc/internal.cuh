@@ -35,8 +35,14 @@ void fill_eps_table(gksl_ctx *c, double t0, double h, long long n);
 void check_drive_grid(const gksl_ctx *c, long long spp, double h);
 // `count` RK4 steps on the context state starting at global step `first` (drive table index)
 void advance(gksl_ctx *c, int precision, double h, long long first, long long count);
-// stages 1-3 of step g from y1 (FP64: double*, FP32: float*), writing the stage inputs Y2, Y3, Y4
-void forward_stage_inputs(gksl_ctx *c, int precision, double h, long long g, void *y1, void *Y2, void *Y3, void *Y4);
+// one CSR-form RK4 step on the context state at step *step_base + local, writing its stage inputs
+// Y2, Y3, Y4 (FP64: double*, FP32: float*; each D + 1 long with 1 at index D) instead of the
+// context's work vectors
+void step_into(gksl_ctx *c, int precision, double h, long long local, void *Y2, void *Y3, void *Y4);
+// device-side step counter base read by the stage kernels (and graphs of them)
+void set_step_base(gksl_ctx *c, long long g);
+// theta(t) (the drive shape without its amplitude) at the three stage times of steps [0, n)
+void fill_theta_table(gksl_ctx *c, double t0, double h, long long n, double *tab);
 void to_f32(const double *v, float *o, long long n, cudaStream_t s);
 
 // ---- mfree.cu (matrix-free stages, GKSL_ASM_MATRIX_FREE)

@@ -279,45 +279,73 @@ Launch make_launch(gksl_ctx *c, const Hyb<double> &h0, double h, const double *t
     return L;
 }
 
+// One RK4 step; the stage inputs go to y2, y3, y4 (y4 may alias y2: the default buffers are
+// yA, yB, yA).
 template <int W>
-void step64_w(gksl_ctx *c, const Launch &L) {
+void step64_w(gksl_ctx *c, const Launch &L, double *y2, double *y3, double *y4) {
     auto A0 = view(c->hyb0), A1 = view(c->hyb1);
     cudaStream_t s = c->stream;
-    k_stage64<1, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v.p, c->v.p, c->yA.p, c->acc.p);
-    k_stage64<2, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yA.p, c->v.p, c->yB.p, c->acc.p);
-    k_stage64<3, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yB.p, c->v.p, c->yA.p, c->acc.p);
-    k_stage64<4, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yA.p, c->v.p, nullptr, c->acc.p);
+    k_stage64<1, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v.p, c->v.p, y2, c->acc.p);
+    k_stage64<2, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v.p, y3, c->acc.p);
+    k_stage64<3, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v.p, y4, c->acc.p);
+    k_stage64<4, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v.p, nullptr, c->acc.p);
 }
 
 template <int W>
-void step32_w(gksl_ctx *c, const Launch &L) {
+void step32_w(gksl_ctx *c, const Launch &L, float *y2, float *y3, float *y4) {
     auto A0 = view(c->hyb0f), A1 = view(c->hyb1f);
     cudaStream_t s = c->stream;
-    k_stage32<1, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v32.p, c->v32.p, c->v.p, c->yA32.p, c->acc32.p);
-    k_stage32<2, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yA32.p, c->v32.p, c->v.p, c->yB32.p, c->acc32.p);
-    k_stage32<3, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yB32.p, c->v32.p, c->v.p, c->yA32.p, c->acc32.p);
-    k_stage32<4, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->yA32.p, c->v32.p, c->v.p, nullptr, c->acc32.p);
+    k_stage32<1, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v32.p, c->v32.p, c->v.p, y2, c->acc32.p);
+    k_stage32<2, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v32.p, c->v.p, y3, c->acc32.p);
+    k_stage32<3, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v32.p, c->v.p, y4, c->acc32.p);
+    k_stage32<4, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v32.p, c->v.p, nullptr, c->acc32.p);
 }
 
 // variants 1 and 2 on either precision
 template <int VAR, int W, typename VT>
-void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h1, VT *v, double *v64, VT *ya, VT *yb,
-              VT *acc) {
+void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h1, VT *v, double *v64, VT *y2, VT *y3,
+              VT *y4, VT *acc) {
     auto A0 = view(h0), A1 = view(h1);
     cudaStream_t s = c->stream;
     Launch L = L0;
     if (VAR == 2) L.grid = (unsigned)(L.a.nb_long + (c->D + 2 * kThreads - 1) / (2 * kThreads));
     if constexpr (VAR == 1) {
-        k_stage_pf<1, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, ya, acc);
-        k_stage_pf<2, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, ya, v, v64, yb, acc);
-        k_stage_pf<3, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, yb, v, v64, ya, acc);
-        k_stage_pf<4, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, ya, v, v64, nullptr, acc);
+        k_stage_pf<1, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
+        k_stage_pf<2, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
+        k_stage_pf<3, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, v, v64, y4, acc);
+        k_stage_pf<4, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, v, v64, nullptr, acc);
     } else {
-        k_stage_r2<1, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, ya, acc);
-        k_stage_r2<2, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, ya, v, v64, yb, acc);
-        k_stage_r2<3, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, yb, v, v64, ya, acc);
-        k_stage_r2<4, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, ya, v, v64, nullptr, acc);
+        k_stage_r2<1, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
+        k_stage_r2<2, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
+        k_stage_r2<3, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, v, v64, y4, acc);
+        k_stage_r2<4, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, v, v64, nullptr, acc);
     }
+}
+
+// CSR-form step with explicit stage-input buffers (null: the context's yA, yB, yA)
+void launch_step_csr(gksl_ctx *c, int precision, double h, const double *tab, long long local, void *Y2, void *Y3,
+                     void *Y4) {
+    Launch L = make_launch(c, c->hyb0, h, tab, local);
+    int W = c->hyb0.width;
+    int var = c->rk4_var[precision == 64 ? 0 : 1];
+    if (var == 1 && W != 18) var = 0;   // the register-prefetch variant exists for the 18-slot layout only
+    if (precision == 64) {
+        double *y2 = Y2 ? (double *)Y2 : c->yA.p, *y3 = Y3 ? (double *)Y3 : c->yB.p, *y4 = Y4 ? (double *)Y4 : c->yA.p;
+        if (var == 1) step_var<1, 18, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
+        else if (var == 2 && W == 18) step_var<2, 18, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
+        else if (var == 2) step_var<2, 0, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
+        else if (W == 18) step64_w<18>(c, L, y2, y3, y4);
+        else step64_w<0>(c, L, y2, y3, y4);
+    } else {
+        float *y2 = Y2 ? (float *)Y2 : c->yA32.p, *y3 = Y3 ? (float *)Y3 : c->yB32.p, *y4 = Y4 ? (float *)Y4 : c->yA32.p;
+        if (var == 1) step_var<1, 18, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
+        else if (var == 2 && W == 18)
+            step_var<2, 18, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
+        else if (var == 2) step_var<2, 0, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
+        else if (W == 18) step32_w<18>(c, L, y2, y3, y4);
+        else step32_w<0>(c, L, y2, y3, y4);
+    }
+    GK_LAUNCH_CHECK();
 }
 
 void launch_step(gksl_ctx *c, int precision, double h, const double *tab, long long local) {
@@ -325,27 +353,7 @@ void launch_step(gksl_ctx *c, int precision, double h, const double *tab, long l
         mf_step(c, precision, h, tab, local);
         return;
     }
-    Launch L = make_launch(c, c->hyb0, h, tab, local);
-    int W = c->hyb0.width;
-    int var = c->rk4_var[precision == 64 ? 0 : 1];
-    if (var == 1 && W != 18) var = 0;   // the register-prefetch variant exists for the 18-slot layout only
-    if (precision == 64) {
-        if (var == 1) step_var<1, 18, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, c->yA.p, c->yB.p, c->acc.p);
-        else if (var == 2 && W == 18)
-            step_var<2, 18, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, c->yA.p, c->yB.p, c->acc.p);
-        else if (var == 2) step_var<2, 0, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, c->yA.p, c->yB.p, c->acc.p);
-        else if (W == 18) step64_w<18>(c, L);
-        else step64_w<0>(c, L);
-    } else {
-        if (var == 1) step_var<1, 18, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, c->yA32.p, c->yB32.p, c->acc32.p);
-        else if (var == 2 && W == 18)
-            step_var<2, 18, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, c->yA32.p, c->yB32.p, c->acc32.p);
-        else if (var == 2)
-            step_var<2, 0, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, c->yA32.p, c->yB32.p, c->acc32.p);
-        else if (W == 18) step32_w<18>(c, L);
-        else step32_w<0>(c, L);
-    }
-    GK_LAUNCH_CHECK();
+    launch_step_csr(c, precision, h, tab, local, nullptr, nullptr, nullptr);
 }
 
 // Time the stage-kernel variants on this context's matrix (a few steps each, from a saved
@@ -507,26 +515,21 @@ void to_f32(const double *v, float *o, long long n, cudaStream_t s) {
     GK_LAUNCH_CHECK();
 }
 
-void forward_stage_inputs(gksl_ctx *c, int precision, double h, long long g, void *y1, void *Y2, void *Y3, void *Y4) {
+void step_into(gksl_ctx *c, int precision, double h, long long local, void *Y2, void *Y3, void *Y4) {
+    GK_REQUIRE(!(c->asm_flags & GKSL_ASM_MATRIX_FREE), GKSL_ERR_STATE, "stage inputs need the CSR form");
+    launch_step_csr(c, precision, h, c->eps_tab.p, local, Y2, Y3, Y4);
+}
+
+void set_step_base(gksl_ctx *c, long long g) {
     k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, g);
     GK_LAUNCH_CHECK();
-    cudaStream_t s = c->stream;
-    if (precision == 64) {
-        Launch L = make_launch(c, c->hyb0, h, c->eps_tab.p, 0);
-        auto A0 = view(c->hyb0), A1 = view(c->hyb1);
-        double *v = (double *)y1;
-        k_stage64<1, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, (double *)Y2, c->acc.p);
-        k_stage64<2, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, (double *)Y2, v, (double *)Y3, c->acc.p);
-        k_stage64<3, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, (double *)Y3, v, (double *)Y4, c->acc.p);
-    } else {
-        Launch L = make_launch(c, c->hyb0, h, c->eps_tab.p, 0);
-        auto A0 = view(c->hyb0f), A1 = view(c->hyb1f);
-        float *v = (float *)y1;
-        k_stage32<1, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, nullptr, (float *)Y2, c->acc32.p);
-        k_stage32<2, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, (float *)Y2, v, nullptr, (float *)Y3, c->acc32.p);
-        k_stage32<3, 0><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, (float *)Y3, v, nullptr, (float *)Y4, c->acc32.p);
+}
+
+void fill_theta_table(gksl_ctx *c, double t0, double h, long long n, double *tab) {
+    if (n > 0) {
+        k_eps_table<<<grid_for(n, 256), 256, 0, c->stream>>>(t0, h, 1.0, c->omega, c->drive_shape, n, tab);
+        GK_LAUNCH_CHECK();
     }
-    GK_LAUNCH_CHECK();
 }
 
 void propagate(gksl_ctx *c, long long spp, long long n_steps, int precision, long long corr_every,
