@@ -210,6 +210,9 @@ def main():
                     help="profiling case for ncu: the N=1000 matrix-free form, 20 FP64 and 20 FP32 RK4 steps")
     ap.add_argument("--profile-batch", action="store_true",
                     help="profiling case for ncu: the 256-instance batch, 40 steps per group")
+    ap.add_argument("--profile-adjoint", action="store_true",
+                    help="profiling case for ncu: one FP64 adjoint gradient of the N=1000 dimer over a "
+                         "period of 64 stable steps (drive frequency raised accordingly)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -223,6 +226,9 @@ def main():
         return
     if args.profile_mf:
         run_profile_mf()
+        return
+    if args.profile_adjoint:
+        run_profile_adjoint()
         return
 
     import torch
@@ -442,6 +448,33 @@ def run_profile_batch():
     G.gksl_batch_destroy(b)
     for c in ctxs:
         G.gksl_destroy(c)
+
+
+def run_profile_adjoint():
+    """Small, fixed case for ncu: the FP64 adjoint of the N = 1000 dimer (every matrix stream
+    larger than L2, about 1.5 GB on the device) over one period of 64 steps.  The drive frequency
+    is raised so that 64 steps are the stable step count (h at the stability bound, as in the
+    full-size runs), which keeps the case short without changing any kernel's work per step."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import numpy as np
+    from paper_1812_11626_gb300 import gksl as G
+    from paper_1812_11626_gb300 import workloads as W
+    d = W.dimer(N_BENCH)
+    ctx = G.dimer_context(d)
+    spp = G.gksl_min_stable_steps(ctx)
+    omega = d.params["omega"] * spp / 64.0
+    G.gksl_set_drive(ctx, d.params["E"], d.params["A"], omega)
+    G.gksl_assemble(ctx, G.GKSL_ASM_FP32 | G.GKSL_ASM_TRANSPOSE)
+    G.gksl_set_rho0(ctx, d.rho0_dense().real.copy(), d.rho0_dense().imag.copy())
+    S = G.gksl_min_stable_steps(ctx)
+    grad = np.zeros(4)
+    t0 = time.perf_counter()
+    loss = G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, 1, 64, grad)
+    el = time.perf_counter() - t0
+    print(json.dumps({"profile_case": "adjoint N=1000", "steps_per_period": S, "omega": omega, "seconds": el,
+                      "loss": loss, "grad": list(grad)}), flush=True)
+    G.gksl_destroy(ctx)
 
 
 def batched_and_adjoint(G, W, torch):

@@ -154,3 +154,54 @@ def test_adjoint_ragged_segments_vs_oracle(G, precision, tol):
         assert np.array_equal(grad, grad2)
     finally:
         G.gksl_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 2e-3)])
+def test_adjoint_general_operators_vs_oracle(G, precision, tol):
+    """Three H0 components, a drive operator and two dissipators (six gradient channels, more
+    than the four-channel kernel holds), with gaps in the component and channel indices; the
+    oracle side unfolds each operator by the definition Tr(F_s L(F_m)) on dense matrices."""
+    from oracle import basis as OB
+    from oracle import lindblad as LB
+    N = 4
+    Hs = [W.random_operator(N, 0.7, 80 + k, hermitian=True) for k in range(3)]
+    H1 = W.random_operator(N, 0.6, 90, hermitian=True)
+    Ls = [W.random_operator(N, 0.6, 91), W.random_operator(N, 0.6, 92)]
+    theta, comps = [0.7, -0.4, 1.1], [0, 2, 5]
+    gam, chans = [0.3, 0.15], [0, 3]
+    E, A, omega = 0.3, 0.8, 2.0
+    S, period = 42, 2
+    o_diag = np.linspace(-1.0, 2.0, N)
+    rho0 = np.diag(np.linspace(1, 3, N)).astype(complex)
+    rho0 /= np.trace(rho0)
+    rho0[0, 2] = 0.05 + 0.02j
+    rho0[2, 0] = np.conj(rho0[0, 2])
+    ctx = G.gksl_create(N)
+    try:
+        for k, th, H in zip(comps, theta, Hs):
+            G.set_csr_operator(G.gksl_set_h0_component, ctx, k, th, op=H)
+        G.set_csr_operator(G.gksl_set_h1, ctx, op=H1)
+        for p, g, L in zip(chans, gam, Ls):
+            G.set_csr_operator(G.gksl_set_dissipator, ctx, p, g, op=L)
+        G.gksl_set_drive(ctx, E, A, omega)
+        G.gksl_assemble(ctx, G.GKSL_ASM_FP32 | G.GKSL_ASM_TRANSPOSE)
+        G.gksl_set_rho0(ctx, rho0.real.copy(), rho0.imag.copy())
+        grad = np.zeros(6)   # [A, gamma_0, gamma_3, theta_0, theta_2, theta_5]
+        loss = G.gksl_adjoint_timeavg(ctx, o_diag, S, period, precision, grad)
+    finally:
+        G.gksl_destroy(ctx)
+    Z = np.zeros((N, N))
+    Qk = [LB.unfold_dense(H.to_dense())[0] for H in Hs]
+    Q1 = LB.unfold_dense(H1.to_dense())[0]
+    RK = [LB.unfold_dense(Z, [L.to_dense()], [1.0]) for L in Ls]
+    Q0 = sum(th * Q for th, Q in zip(theta, Qk)) + sum(g * R for g, (R, _) in zip(gam, RK))
+    K = sum(g * Kp for g, (_, Kp) in zip(gam, RK))
+    w, c0 = OP.observable_weights(o_diag)
+    v0 = OB.expand(rho0).real
+    h = 2 * np.pi / omega / S
+    sinw = lambda t: np.sin(omega * t)
+    L_ref, g_ref = OP.timeavg_adjoint(Q0, Q1, K, OP.eps_fn(E, A, omega), v0, w, c0, h, S, period,
+                                      dQ0=[None, RK[0][0], RK[1][0]] + Qk, dQ1=[(Q1, sinw)] + [None] * 5,
+                                      dK=[None, RK[0][1], RK[1][1]] + [None] * 3)
+    assert abs(loss - L_ref) < (1e-11 if precision == 64 else 1e-4) * max(1.0, abs(L_ref))
+    assert np.abs(grad - g_ref).max() < tol * np.abs(g_ref).max(), (grad, g_ref)

@@ -244,3 +244,72 @@ def test_config4_n1000_fp64_steps(G):
         assert np.abs(o32[0] - v_ref).max() < TOL32_V
     finally:
         G.gksl_destroy(ctx)
+
+
+def _oracle_system(H0, H1, Ls, gammas):
+    """(Q0, Q1, K) by the definition Tr(F_s L(F_m)) on dense matrices (Q1 = 0 without H1)."""
+    N = H0.shape[0]
+    Q0, K = OL.unfold_dense(H0, Ls, gammas)
+    Q1 = OL.unfold_dense(H1)[0] if H1 is not None else np.zeros_like(Q0)
+    return Q0, Q1, K
+
+
+def test_smallest_and_degenerate_systems(G):
+    """N = 2 (D = 3: one S, one J, one D generator) with a drive and a decay channel; N = 3 with
+    no drive operator and no dissipator (pure Hamiltonian: |v| conserved up to RK4's h^5 loss);
+    and zero steps, which leave state and time as they were."""
+    # qubit: H0 = (w0/2) sz, H1 = sx, L = sigma_minus at rate 0.2
+    w0, E, A, omega, gam = 1.7, 0.1, 0.5, 1.3, 0.2
+    H0 = np.diag([0.5 * w0, -0.5 * w0]).astype(complex)
+    H1 = np.array([[0, 1], [1, 0]], dtype=complex)
+    L = np.array([[0, 1], [0, 0]], dtype=complex)
+    rho0 = np.array([[0.3, 0.2 - 0.1j], [0.2 + 0.1j, 0.7]])
+    ctx = G.gksl_create(2)
+    try:
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 1.0, op=W.CSR.from_dense(H0))
+        G.set_csr_operator(G.gksl_set_h1, ctx, op=W.CSR.from_dense(H1))
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, gam, op=W.CSR.from_dense(L))
+        G.gksl_set_drive(ctx, E, A, omega)
+        G.gksl_assemble(ctx, G.GKSL_ASM_FP32)
+        G.gksl_set_rho0(ctx, rho0.real.copy(), rho0.imag.copy())
+        spp, n, emit = 100, 250, 50
+        # zero steps: nothing moves
+        v_before = np.zeros(3)
+        t_before = G.gksl_get_state(ctx, v_before)
+        G.gksl_propagate(ctx, spp, 0, 64, 0, 0, None)
+        v_after = np.zeros(3)
+        assert G.gksl_get_state(ctx, v_after) == t_before
+        assert np.array_equal(v_before, v_after)
+        out = run_gpu(G, ctx, spp, n, emit, D=3)
+        Q0, Q1, K = _oracle_system(H0, H1, [L], [gam])
+        h = 2 * np.pi / omega / spp
+        _, ref = OP.rk4(Q0, Q1, K, OP.eps_fn(E, A, omega), OB.expand(rho0).real, h, n, emit_every=emit)
+        assert max(np.abs(out[i] - ref[i]).max() for i in range(len(ref))) < TOL64
+    finally:
+        G.gksl_destroy(ctx)
+    # N = 3, Hamiltonian only, no H1
+    H = W.random_operator(3, 0.8, 33, hermitian=True)
+    rho0 = np.diag([0.5, 0.3, 0.2]).astype(complex)
+    rho0[0, 1] = rho0[1, 0] = 0.1
+    ctx = G.gksl_create(3)
+    try:
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 1.0, op=H)
+        G.gksl_set_drive(ctx, 0.0, 0.0, 1.0)
+        G.gksl_assemble(ctx, 0)
+        G.gksl_set_rho0(ctx, rho0.real.copy(), rho0.imag.copy())
+        spp, n = 400, 800
+        out = run_gpu(G, ctx, spp, n, n, D=8)
+        Q0, Q1, K = _oracle_system(H.to_dense(), None, [], [])
+        v0 = OB.expand(rho0).real
+        h = 2 * np.pi / spp
+        vref, _ = OP.rk4(Q0, Q1, K, OP.eps_fn(0.0, 0.0, 1.0), v0, h, n)
+        assert np.abs(out[0] - vref).max() < TOL64
+        # Q0 is skew (unitary evolution): each eigenmode of frequency y/h shrinks by |R(iy)| per
+        # step with |R(iy)|^2 = 1 - y^6/72 + y^8/576 (RK4's stability function on the imaginary
+        # axis), so |v0| |R(i h rho)|^n <= |v(t)| <= |v0| with rho the largest |eigenvalue|
+        y = h * np.abs(np.linalg.eigvals(Q0)).max()
+        shrink = np.sqrt(1 - y ** 6 / 72 + y ** 8 / 576) ** n
+        nv, n0 = np.linalg.norm(out[0]), np.linalg.norm(v0)
+        assert n0 * shrink - 1e-13 <= nv <= n0 + 1e-13, (nv, n0, shrink)
+    finally:
+        G.gksl_destroy(ctx)
