@@ -235,6 +235,7 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_1812_11626_gb300 import gksl as G
+    from paper_1812_11626_gb300 import replicas as R
     from paper_1812_11626_gb300 import workloads as W
 
     torch.cuda.set_device(local)
@@ -274,12 +275,9 @@ def main():
     barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
-    ms_all = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = world * args.steps * STEP_RK4 / (ms_all * 1e-3)
+    # every rank runs its own replica: RK4 steps of all ranks over the slowest rank's time
+    ms_all, total_steps = R.reduce_timing(ms, args.steps * STEP_RK4, dist, "cuda")
+    value = total_steps / (ms_all * 1e-3)
     avg_launch_ms = ms / (args.steps * STEP_RK4 * 4)
     bytes_launch = stage_bytes(info.nnz_q0, info.nnz_q1, D, 64)
     hbm, peak_kind = peaks()
@@ -300,13 +298,16 @@ def main():
     host_out = torch.empty(D, dtype=torch.float64, pin_memory=True)
     G.gksl_get_state(ctx, host_in.numpy())
     torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         G.gksl_set_state(ctx, host_in, 0.0)
         G.gksl_propagate(ctx, spp, STEP_RK4, 64, 0, STEP_RK4, host_out)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * args.steps * STEP_RK4 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * D,
+    barrier()
+    e2e = {"value": R.throughput(1e3 * e2e_s, args.steps * STEP_RK4, dist, "cuda"), "unit": UNIT,
+           "h2d_bytes_per_step": 8 * D,
            "d2h_bytes_per_step": 8 * D}
 
     extras = {}
