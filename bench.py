@@ -94,17 +94,18 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
-def stage_bytes(nnz0, nnz1, D, precision):
+def stage_bytes(nnz0, nnz1, D, precision, q1_folded=False):
     """Compulsory bytes per RK4 stage launch, averaged over the 4 stages of a step.
 
-    Matrix stream: value + int32 column per stored entry of [Q0 + E Q1 | K] and Q1 (no row
-    pointers in the ELL layout).  Vectors, per step: stage 1 reads v once (also the gather
-    source) and writes y2 and acc; stages 2-3 gather y, read v, write y_next, read+write acc;
-    stage 4 gathers y4, reads+writes v, reads acc: 17 vector passes of D elements, plus the
-    FP64 master update (read+write) of the FP32 form.
+    Matrix stream: value + int32 column per stored entry of [Q0 + E Q1 | K] (no row pointers in
+    the ELL layout) and of Q1; with Q1 folded into the first slot of its row, one Q1 value per
+    row instead.  Vectors, per step: stage 1 reads v once (also the gather source) and writes y2
+    and acc; stages 2-3 gather y, read v, write y_next, read+write acc; stage 4 gathers y4,
+    reads+writes v, reads acc: 17 vector passes of D elements, plus the FP64 master update
+    (read+write) of the FP32 form.
     """
     vb = 8 if precision == 64 else 4
-    mat = (vb + 4) * (nnz0 + nnz1)
+    mat = (vb + 4) * nnz0 + (vb * D if q1_folded else (vb + 4) * nnz1)
     vec = 17 * vb * D + (16 * D if precision == 32 else 0)
     return (4 * mat + vec) / 4.0
 
@@ -279,7 +280,7 @@ def main():
     ms_all, total_steps = R.reduce_timing(ms, args.steps * STEP_RK4, dist, "cuda")
     value = total_steps / (ms_all * 1e-3)
     avg_launch_ms = ms / (args.steps * STEP_RK4 * 4)
-    bytes_launch = stage_bytes(info.nnz_q0, info.nnz_q1, D, 64)
+    bytes_launch = stage_bytes(info.nnz_q0, info.nnz_q1, D, 64, bool(info.q1_folded))
     hbm, peak_kind = peaks()
     achieved = bytes_launch / (avg_launch_ms * 1e-3) / 1e9
     variant = G.gksl_get_info(ctx).rk4_variant[0]
@@ -323,7 +324,7 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         ms32 = f0.elapsed_time(f1)
-        b32 = stage_bytes(info.nnz_q0, info.nnz_q1, D, 32)
+        b32 = stage_bytes(info.nnz_q0, info.nnz_q1, D, 32, bool(info.q1_folded))
         extras["fp32_bulk"] = {"value": args.steps * STEP_RK4 / (ms32 * 1e-3), "unit": UNIT,
                                "achieved_gbs": b32 / (ms32 * 1e-3 / (args.steps * STEP_RK4 * 4)) / 1e9}
         extras["assembly_s"] = asm_s

@@ -130,6 +130,12 @@ gksl_status gksl_structure_enumerate(int N, int which, long long capacity, int *
 #define GKSL_ASM_FP32 1u        /* also build the FP32 copies used by precision 32 */
 #define GKSL_ASM_TRANSPOSE 2u   /* also build the transposes used by the adjoint */
 #define GKSL_ASM_NO_DROP 4u     /* keep entries |q| <= 64 eps max|Q| in Q0 */
+/* Keep Q1 as a separate stream of the RK4 stages.  By default, when every row of Q1 has at most
+ * one entry and that entry's column is among the row's entries of Q0 + E Q1 (a pair rotation,
+ * as for any diagonal H1), Q1 is folded into that slot: the stage forms q0 + (eps(t) - E) q1
+ * there and reads no Q1 column indices.  Both forms compute the same map; they differ by
+ * rounding only. */
+#define GKSL_ASM_NO_FOLD 16u
 /* Matrix-free form: build no CSR matrix; keep H0 (+ E H1), H1, Gamma = 1/2 sum_p gamma_p L_p^+ L_p
  * and sqrt(gamma_p) L_p as complex diagonals (O(N) data) and let gksl_propagate apply Q(t) v + K on
  * the fly, as Tr(F_s L_t(rho)) with rho = 1/N + sum v F (Eq. 1, 6, 8), from tiles of rho rebuilt
@@ -274,6 +280,7 @@ typedef struct {
     double max_abs_q0;
     int rk4_variant[2];           /* stage-kernel variant in use, [0]: FP64, [1]: FP32 (chosen by timing) */
     double rk4_variant_us[2][3];  /* timed cost per RK4 step of each variant, microseconds (0: not timed) */
+    int q1_folded;                /* 1: Q1 folded into the propagation format (see GKSL_ASM_NO_FOLD) */
 } gksl_info;
 
 gksl_status gksl_get_info(gksl_ctx *ctx, gksl_info *out);

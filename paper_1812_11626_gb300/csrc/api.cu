@@ -646,6 +646,7 @@ extern "C" gksl_status gksl_get_info(gksl_ctx *c, gksl_info *out) {
         out->ell_width_q1 = c->hyb1.width;
         out->long_rows = c->hyb0.n_long;
         size_t b = c->Q0.bytes() + c->Q1.bytes() + c->K.bytes() + c->hyb0.bytes() + c->hyb1.bytes() + c->hyb0f.bytes() +
+                   c->q1v.bytes() + c->q1vf.bytes() +
                    c->hyb1f.bytes() + c->v.bytes() + c->yA.bytes() + c->yB.bytes() + c->acc.bytes() + c->v32.bytes() +
                    c->yA32.bytes() + c->yB32.bytes() + c->acc32.bytes() + c->eps_tab.bytes();
         for (int k = 0; k < GKSL_MAX_H0; ++k) b += c->QH0[k].bytes();
@@ -658,6 +659,7 @@ extern "C" gksl_status gksl_get_info(gksl_ctx *c, gksl_info *out) {
         out->device_bytes = (long long)b;
         out->assemble_seconds = c->assemble_seconds;
         out->max_abs_q0 = c->max_abs_q0;
+        out->q1_folded = c->q1_folded ? 1 : 0;
         for (int p = 0; p < 2; ++p) {
             out->rk4_variant[p] = c->rk4_var[p];
             for (int v = 0; v < 3; ++v) out->rk4_variant_us[p][v] = c->rk4_var_us[p][v];

@@ -523,6 +523,9 @@ void assemble(gksl_ctx *c, unsigned flags) {
         c->hyb1 = Hyb<double>();
         c->hyb0f = Hyb<float>();
         c->hyb1f = Hyb<float>();
+        c->q1_folded = false;
+        c->q1v.release();
+        c->q1vf.release();
         for (int i = 0; i < gksl_ctx::kMaxCh; ++i) {
             c->adj[i] = Hyb<double>();
             c->adjf[i] = Hyb<float>();
@@ -585,6 +588,8 @@ void assemble(gksl_ctx *c, unsigned flags) {
     c->nnz_q0e = q0e.nnz;
     bool fp32 = (flags & GKSL_ASM_FP32) != 0;
     build_hyb_pair(q0e, c->Q1, D, c->hyb0, c->hyb1, fp32 ? &c->hyb0f : nullptr, fp32 ? &c->hyb1f : nullptr, s);
+    c->q1_folded = !(flags & GKSL_ASM_NO_FOLD) &&
+                   fold_q1(q0e, c->Q1, D, c->hyb0, fp32 ? &c->hyb0f : nullptr, c->q1v, c->q1vf, s);
     c->has_adj = false;
     c->adj_n = 0;
     if (flags & GKSL_ASM_TRANSPOSE) {

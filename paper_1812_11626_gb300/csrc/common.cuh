@@ -198,6 +198,12 @@ struct gksl_ctx {
     long long nnz_q0e = 0;
     gk::Hyb<double> hyb0, hyb1;   // propagation format of [Q0 + E Q1 | K] and Q1
     gk::Hyb<float> hyb0f, hyb1f;  // FP32 copies
+    // Q1 folded into slot 0 of hyb0 (every short row has at most one Q1 entry, at a column of
+    // its [Q0 + E Q1] row, moved to slot 0): the stage takes slot 0 as q0 + (eps - E) q1 and
+    // reads no Q1 ELL; q1v[r] is that Q1 value (0 without one), long rows keep the Q1 tails
+    bool q1_folded = false;
+    gk::DBuf<double> q1v;
+    gk::DBuf<float> q1vf;
     gk::MfBands mf;               // matrix-free form (GKSL_ASM_MATRIX_FREE)
     // adjoint: one channel per parameter matrix, transposed (Q(H)^T = -Q(H) is stored negated),
     // all channels sharing one long-row set: H0 components, then Q1, then the dissipators

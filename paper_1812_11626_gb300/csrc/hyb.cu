@@ -181,7 +181,90 @@ void build_set(const std::vector<const CsrR *> &ms, const std::vector<double> &s
     GK_CUDA(cudaStreamSynchronize(s));
 }
 
+// Rows that keep Q1 out of slot 0: more than one Q1 entry, or its column missing from the
+// row's [Q0 + E Q1] entries with no free slot to add it (long rows keep Q1 in the tails and are
+// skipped).  The column can be missing where q0 + E q1 cancels and was dropped as a numerical
+// zero; that leaves a free slot.
+__global__ void k_q1_fold_check(const int *__restrict__ q0_rowptr, const int *__restrict__ q1_rowptr,
+                                const int *__restrict__ q1_col, const int *__restrict__ ell_col, long long ld, int W,
+                                long long rows, int *__restrict__ bad) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int n1 = q1_rowptr[r + 1] - q1_rowptr[r];
+    if (n1 == 0 || ell_col[r] < 0) return;
+    if (n1 > 1) {
+        atomicOr(bad, 1);
+        return;
+    }
+    const int c1 = q1_col[q1_rowptr[r]];
+    const int len = q0_rowptr[r + 1] - q0_rowptr[r];
+    for (int j = 0; j < len; ++j)
+        if (ell_col[(long long)j * ld + r] == c1) return;
+    if (len >= W) atomicOr(bad, 1);
+}
+
+// Move the entry at Q1's column to slot 0 of each short row (adding it with value 0 in the
+// first free slot when it was dropped) and record Q1's value there.
+template <typename VT>
+__global__ void k_q1_fold(const int *__restrict__ q0_rowptr, const int *__restrict__ q1_rowptr,
+                          const int *__restrict__ q1_col, const double *__restrict__ q1_val, long long ld,
+                          long long rows, int *__restrict__ ell_col, VT *__restrict__ ell_val, VT *__restrict__ q1v) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ld) return;
+    q1v[r] = VT(0);
+    if (r >= rows || ell_col[r] < 0) return;
+    const int n1 = q1_rowptr[r + 1] - q1_rowptr[r];
+    if (n1 == 0) return;
+    const int c1 = q1_col[q1_rowptr[r]];
+    const int len = q0_rowptr[r + 1] - q0_rowptr[r];
+    int found = -1;
+    for (int j = 0; j < len && found < 0; ++j)
+        if (ell_col[(long long)j * ld + r] == c1) found = j;
+    if (found < 0) {   // the free slot `len` exists (checked by k_q1_fold_check)
+        found = len;
+        ell_col[(long long)len * ld + r] = c1;
+        ell_val[(long long)len * ld + r] = VT(0);
+    }
+    const long long p = (long long)found * ld + r;
+    const int tc = ell_col[r];
+    const VT tv = ell_val[r];
+    ell_col[r] = ell_col[p];
+    ell_val[r] = ell_val[p];
+    ell_col[p] = tc;
+    ell_val[p] = tv;
+    q1v[r] = (VT)q1_val[q1_rowptr[r]];
+}
+
 }  // namespace
+
+bool fold_q1(const CsrR &q0e, const CsrR &q1, long long rows, Hyb<double> &h0, Hyb<float> *h0f, DBuf<double> &q1v,
+             DBuf<float> &q1vf, cudaStream_t s) {
+    q1v.release();
+    q1vf.release();
+    if (q1.nnz == 0 || h0.width < 1) return false;
+    DBuf<int> bad(1);
+    GK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+    k_q1_fold_check<<<grid_for(rows, 256), 256, 0, s>>>(q0e.rowptr.p, q1.rowptr.p, q1.col.p, h0.ell_col.p, h0.ld,
+                                                          h0.width, rows, bad.p);
+    GK_LAUNCH_CHECK();
+    int hbad = 0;
+    GK_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return false;
+    q1v.alloc((size_t)h0.ld);
+    k_q1_fold<double><<<grid_for(h0.ld, 256), 256, 0, s>>>(q0e.rowptr.p, q1.rowptr.p, q1.col.p, q1.val.p, h0.ld, rows,
+                                                            h0.ell_col.p, h0.ell_val.p, q1v.p);
+    GK_LAUNCH_CHECK();
+    if (h0f) {
+        q1vf.alloc((size_t)h0f->ld);
+        k_q1_fold<float><<<grid_for(h0f->ld, 256), 256, 0, s>>>(q0e.rowptr.p, q1.rowptr.p, q1.col.p, q1.val.p,
+                                                                 h0f->ld, rows, h0f->ell_col.p, h0f->ell_val.p,
+                                                                 q1vf.p);
+        GK_LAUNCH_CHECK();
+    }
+    GK_CUDA(cudaStreamSynchronize(s));
+    return true;
+}
 
 void build_hyb_pair(const CsrR &a0, const CsrR &a1, long long rows, Hyb<double> &h0, Hyb<double> &h1, Hyb<float> *h0f,
                     Hyb<float> *h1f, cudaStream_t s) {

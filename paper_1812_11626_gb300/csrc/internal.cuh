@@ -66,6 +66,10 @@ long long structure_enumerate(int N, int which, long long cap, int *m, int *n, i
 void build_hyb_pair(const CsrR &a0, const CsrR &a1, long long rows, Hyb<double> &h0, Hyb<double> &h1,
                     Hyb<float> *h0f, Hyb<float> *h1f, cudaStream_t s);
 void build_hyb_single(const CsrR &a, long long rows, Hyb<double> &h, Hyb<float> *hf, double scale, cudaStream_t s);
+// Fold Q1 into slot 0 of the propagation ELL of q0e = [Q0 + E Q1 | K] when every short row has
+// at most one Q1 entry and its column is among the row's entries; returns whether it did
+bool fold_q1(const CsrR &q0e, const CsrR &q1, long long rows, Hyb<double> &h0, Hyb<float> *h0f, DBuf<double> &q1v,
+             DBuf<float> &q1vf, cudaStream_t s);
 // several matrices applied together (one long-row set; entries scaled by `scales`)
 void build_hyb_multi(const std::vector<const CsrR *> &ms, const std::vector<double> &scales, long long rows,
                      const std::vector<Hyb<double> *> &out, const std::vector<Hyb<float> *> &outf, cudaStream_t s);

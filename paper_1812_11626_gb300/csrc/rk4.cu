@@ -93,9 +93,19 @@ struct StepArgs {
     const long long *base;
     long long local;
     HConst hc;
+    const double *q1v;    // Q1 folded into slot 0 (M kernels): its value per row
+    const float *q1vf;
 };
 
-template <int STAGE, int W>
+template <typename VT>
+__device__ inline const VT *q1_of(const StepArgs &a);
+template <>
+__device__ inline const double *q1_of<double>(const StepArgs &a) { return a.q1v; }
+template <>
+__device__ inline const float *q1_of<float>(const StepArgs &a) { return a.q1vf; }
+
+// M: Q1 folded into slot 0 (slot 0 holds q0 + (eps - E) q1, no Q1 ELL is read)
+template <int STAGE, int W, bool M>
 __global__ void __launch_bounds__(kThreads) k_stage64(HybView<double> A0, HybView<double> A1, StepArgs a,
                                                       const double *__restrict__ y, double *v, double *__restrict__ yn,
                                                       double *__restrict__ acc) {
@@ -117,12 +127,13 @@ __global__ void __launch_bounds__(kThreads) k_stage64(HybView<double> A0, HybVie
     int c0 = ldcs(A0.ell_col + r);
     if (c0 < 0) return;   // long row, handled by a warp above
     double a0 = ldcs(A0.ell_val + r);
+    if (M) a0 = fma(eps, ldcs(a.q1v + r), a0);
     double s0 = ell_dot<double, double, W>(A0, r, c0, a0, y);
-    double s1 = ell_dot_full<double, double>(A1, r, y);
-    epi64<STAGE>(r, s0 + eps * s1, v, yn, acc, a.hc);
+    if (!M) s0 = s0 + eps * ell_dot_full<double, double>(A1, r, y);
+    epi64<STAGE>(r, s0, v, yn, acc, a.hc);
 }
 
-template <int STAGE, int W>
+template <int STAGE, int W, bool M>
 __global__ void __launch_bounds__(kThreads) k_stage32(HybView<float> A0, HybView<float> A1, StepArgs a,
                                                       const float *__restrict__ y, float *v32, double *v64,
                                                       float *__restrict__ yn, float *__restrict__ acc) {
@@ -144,9 +155,10 @@ __global__ void __launch_bounds__(kThreads) k_stage32(HybView<float> A0, HybView
     int c0 = ldcs(A0.ell_col + r);
     if (c0 < 0) return;
     float a0 = ldcs(A0.ell_val + r);
+    if (M) a0 = fmaf(eps, ldcs(a.q1vf + r), a0);
     float s0 = ell_dot<float, float, W>(A0, r, c0, a0, y);
-    float s1 = ell_dot_full<float, float>(A1, r, y);
-    epi32<STAGE>(r, s0 + eps * s1, v32, v64, yn, acc, a.hc);
+    if (!M) s0 = s0 + eps * ell_dot_full<float, float>(A1, r, y);
+    epi32<STAGE>(r, s0, v32, v64, yn, acc, a.hc);
 }
 
 // ---- variants of the ELL part (same arithmetic, same summation order per row)
@@ -167,7 +179,7 @@ __device__ inline bool long_rows_part(const HybView<VT> &A0, const HybView<VT> &
 
 // Variant 1: the whole ELL row is loaded into registers (all columns, then all values, then
 // all gathers) before the products, with a larger register budget for the loads in flight.
-template <int STAGE, int W, typename VT>
+template <int STAGE, int W, typename VT, bool M>
 __global__ void __launch_bounds__(kThreads, 3) k_stage_pf(HybView<VT> A0, HybView<VT> A1, StepArgs a,
                                                           const VT *__restrict__ y, VT *v, double *v64,
                                                           VT *__restrict__ yn, VT *__restrict__ acc) {
@@ -185,18 +197,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_stage_pf(HybView<VT> A0, HybVie
     if (c[0] < 0) return;
 #pragma unroll
     for (int j = 0; j < W; ++j) m[j] = ldcs(A0.ell_val + (long long)j * A0.ld + r);
+    if (M) m[0] = eps * ldcs(q1_of<VT>(a) + r) + m[0];
 #pragma unroll
     for (int j = 0; j < W; ++j) x[j] = __ldg(y + c[j]);
     VT s0 = m[0] * x[0];
 #pragma unroll
     for (int j = 1; j < W; ++j) s0 += m[j] * x[j];
-    VT s1 = ell_dot_full<VT, VT>(A1, r, y);
-    epi<STAGE, VT>(r, s0 + eps * s1, v, v64, yn, acc, a.hc);
+    if (!M) s0 = s0 + eps * ell_dot_full<VT, VT>(A1, r, y);
+    epi<STAGE, VT>(r, s0, v, v64, yn, acc, a.hc);
 }
 
 // Variant 2: two consecutive rows per thread with 2-wide vector loads of the slot-major ELL
 // arrays (ld is a multiple of 32 and r is even, so every vector access is aligned).
-template <int STAGE, int W, typename VT>
+template <int STAGE, int W, typename VT, bool M>
 __global__ void __launch_bounds__(kThreads) k_stage_r2(HybView<VT> A0, HybView<VT> A1, StepArgs a,
                                                        const VT *__restrict__ y, VT *v, double *v64,
                                                        VT *__restrict__ yn, VT *__restrict__ acc) {
@@ -211,6 +224,11 @@ __global__ void __launch_bounds__(kThreads) k_stage_r2(HybView<VT> A0, HybView<V
     const int w0 = W > 0 ? W : A0.width;
     int2 c = ldcs((const int2 *)(A0.ell_col + r));
     V2 m = ldcs((const V2 *)(A0.ell_val + r));
+    if (M) {
+        const V2 q = ldcs((const V2 *)(q1_of<VT>(a) + r));
+        m.x = eps * q.x + m.x;
+        m.y = eps * q.y + m.y;
+    }
     const bool live0 = c.x >= 0, live1 = (r + 1 < a.D) && c.y >= 0;
     VT sa = m.x * __ldg(y + (c.x < 0 ? 0 : c.x));
     VT sb = m.y * __ldg(y + (c.y < 0 ? 0 : c.y));
@@ -223,16 +241,20 @@ __global__ void __launch_bounds__(kThreads) k_stage_r2(HybView<VT> A0, HybView<V
         sa += mj.x * __ldg(y + cj.x);
         sb += mj.y * __ldg(y + cj.y);
     }
-    VT ta = VT(0), tb = VT(0);
-    for (int j = 0; j < A1.width; ++j) {
-        long long p = (long long)j * A1.ld + r;
-        int2 cj = ldcs((const int2 *)(A1.ell_col + p));
-        V2 mj = ldcs((const V2 *)(A1.ell_val + p));
-        ta += mj.x * __ldg(y + cj.x);
-        tb += mj.y * __ldg(y + cj.y);
+    if (!M) {
+        VT ta = VT(0), tb = VT(0);
+        for (int j = 0; j < A1.width; ++j) {
+            long long p = (long long)j * A1.ld + r;
+            int2 cj = ldcs((const int2 *)(A1.ell_col + p));
+            V2 mj = ldcs((const V2 *)(A1.ell_val + p));
+            ta += mj.x * __ldg(y + cj.x);
+            tb += mj.y * __ldg(y + cj.y);
+        }
+        sa = sa + eps * ta;
+        sb = sb + eps * tb;
     }
-    if (live0) epi<STAGE, VT>(r, sa + eps * ta, v, v64, yn, acc, a.hc);
-    if (live1) epi<STAGE, VT>(r + 1, sb + eps * tb, v, v64, yn, acc, a.hc);
+    if (live0) epi<STAGE, VT>(r, sa, v, v64, yn, acc, a.hc);
+    if (live1) epi<STAGE, VT>(r + 1, sb, v, v64, yn, acc, a.hc);
 }
 
 __global__ void k_to_f32(const double *__restrict__ v, float *__restrict__ o, long long n) {
@@ -275,34 +297,36 @@ Launch make_launch(gksl_ctx *c, const Hyb<double> &h0, double h, const double *t
     L.a.hc.hf = (float)h;
     L.a.hc.h2f = 0.5f * (float)h;
     L.a.hc.h6f = (float)(h / 6.0);
+    L.a.q1v = c->q1_folded ? c->q1v.p : nullptr;
+    L.a.q1vf = c->q1_folded ? c->q1vf.p : nullptr;
     L.grid = (unsigned)(L.a.nb_long + (c->D + kThreads - 1) / kThreads);
     return L;
 }
 
 // One RK4 step; the stage inputs go to y2, y3, y4 (y4 may alias y2: the default buffers are
 // yA, yB, yA).
-template <int W>
+template <int W, bool M>
 void step64_w(gksl_ctx *c, const Launch &L, double *y2, double *y3, double *y4) {
     auto A0 = view(c->hyb0), A1 = view(c->hyb1);
     cudaStream_t s = c->stream;
-    k_stage64<1, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v.p, c->v.p, y2, c->acc.p);
-    k_stage64<2, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v.p, y3, c->acc.p);
-    k_stage64<3, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v.p, y4, c->acc.p);
-    k_stage64<4, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v.p, nullptr, c->acc.p);
+    k_stage64<1, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v.p, c->v.p, y2, c->acc.p);
+    k_stage64<2, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v.p, y3, c->acc.p);
+    k_stage64<3, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v.p, y4, c->acc.p);
+    k_stage64<4, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v.p, nullptr, c->acc.p);
 }
 
-template <int W>
+template <int W, bool M>
 void step32_w(gksl_ctx *c, const Launch &L, float *y2, float *y3, float *y4) {
     auto A0 = view(c->hyb0f), A1 = view(c->hyb1f);
     cudaStream_t s = c->stream;
-    k_stage32<1, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v32.p, c->v32.p, c->v.p, y2, c->acc32.p);
-    k_stage32<2, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v32.p, c->v.p, y3, c->acc32.p);
-    k_stage32<3, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v32.p, c->v.p, y4, c->acc32.p);
-    k_stage32<4, W><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v32.p, c->v.p, nullptr, c->acc32.p);
+    k_stage32<1, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v32.p, c->v32.p, c->v.p, y2, c->acc32.p);
+    k_stage32<2, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v32.p, c->v.p, y3, c->acc32.p);
+    k_stage32<3, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v32.p, c->v.p, y4, c->acc32.p);
+    k_stage32<4, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v32.p, c->v.p, nullptr, c->acc32.p);
 }
 
 // variants 1 and 2 on either precision
-template <int VAR, int W, typename VT>
+template <int VAR, int W, typename VT, bool M>
 void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h1, VT *v, double *v64, VT *y2, VT *y3,
               VT *y4, VT *acc) {
     auto A0 = view(h0), A1 = view(h1);
@@ -310,42 +334,51 @@ void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h
     Launch L = L0;
     if (VAR == 2) L.grid = (unsigned)(L.a.nb_long + (c->D + 2 * kThreads - 1) / (2 * kThreads));
     if constexpr (VAR == 1) {
-        k_stage_pf<1, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
-        k_stage_pf<2, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
-        k_stage_pf<3, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, v, v64, y4, acc);
-        k_stage_pf<4, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, v, v64, nullptr, acc);
+        k_stage_pf<1, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
+        k_stage_pf<2, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
+        k_stage_pf<3, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, v, v64, y4, acc);
+        k_stage_pf<4, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, v, v64, nullptr, acc);
     } else {
-        k_stage_r2<1, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
-        k_stage_r2<2, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
-        k_stage_r2<3, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, v, v64, y4, acc);
-        k_stage_r2<4, W, VT><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, v, v64, nullptr, acc);
+        k_stage_r2<1, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
+        k_stage_r2<2, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
+        k_stage_r2<3, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, v, v64, y4, acc);
+        k_stage_r2<4, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, v, v64, nullptr, acc);
     }
 }
 
 // CSR-form step with explicit stage-input buffers (null: the context's yA, yB, yA)
-void launch_step_csr(gksl_ctx *c, int precision, double h, const double *tab, long long local, void *Y2, void *Y3,
-                     void *Y4) {
+template <bool M>
+void launch_step_csr_t(gksl_ctx *c, int precision, double h, const double *tab, long long local, void *Y2, void *Y3,
+                       void *Y4) {
     Launch L = make_launch(c, c->hyb0, h, tab, local);
     int W = c->hyb0.width;
     int var = c->rk4_var[precision == 64 ? 0 : 1];
     if (var == 1 && W != 18) var = 0;   // the register-prefetch variant exists for the 18-slot layout only
     if (precision == 64) {
         double *y2 = Y2 ? (double *)Y2 : c->yA.p, *y3 = Y3 ? (double *)Y3 : c->yB.p, *y4 = Y4 ? (double *)Y4 : c->yA.p;
-        if (var == 1) step_var<1, 18, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
-        else if (var == 2 && W == 18) step_var<2, 18, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
-        else if (var == 2) step_var<2, 0, double>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
-        else if (W == 18) step64_w<18>(c, L, y2, y3, y4);
-        else step64_w<0>(c, L, y2, y3, y4);
+        if (var == 1) step_var<1, 18, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
+        else if (var == 2 && W == 18)
+            step_var<2, 18, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
+        else if (var == 2) step_var<2, 0, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
+        else if (W == 18) step64_w<18, M>(c, L, y2, y3, y4);
+        else step64_w<0, M>(c, L, y2, y3, y4);
     } else {
         float *y2 = Y2 ? (float *)Y2 : c->yA32.p, *y3 = Y3 ? (float *)Y3 : c->yB32.p, *y4 = Y4 ? (float *)Y4 : c->yA32.p;
-        if (var == 1) step_var<1, 18, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
+        if (var == 1) step_var<1, 18, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
         else if (var == 2 && W == 18)
-            step_var<2, 18, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
-        else if (var == 2) step_var<2, 0, float>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
-        else if (W == 18) step32_w<18>(c, L, y2, y3, y4);
-        else step32_w<0>(c, L, y2, y3, y4);
+            step_var<2, 18, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
+        else if (var == 2)
+            step_var<2, 0, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
+        else if (W == 18) step32_w<18, M>(c, L, y2, y3, y4);
+        else step32_w<0, M>(c, L, y2, y3, y4);
     }
     GK_LAUNCH_CHECK();
+}
+
+void launch_step_csr(gksl_ctx *c, int precision, double h, const double *tab, long long local, void *Y2, void *Y3,
+                     void *Y4) {
+    if (c->q1_folded) launch_step_csr_t<true>(c, precision, h, tab, local, Y2, Y3, Y4);
+    else launch_step_csr_t<false>(c, precision, h, tab, local, Y2, Y3, Y4);
 }
 
 void launch_step(gksl_ctx *c, int precision, double h, const double *tab, long long local) {

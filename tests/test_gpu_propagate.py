@@ -313,3 +313,42 @@ def test_smallest_and_degenerate_systems(G):
         assert n0 * shrink - 1e-13 <= nv <= n0 + 1e-13, (nv, n0, shrink)
     finally:
         G.gksl_destroy(ctx)
+
+
+def test_folded_q1_matches_separate_stream(G):
+    """Q1 folded into the propagation format (the default for the dimer, whose H1 is diagonal)
+    against Q1 as a separate stream (GKSL_ASM_NO_FOLD): the same RK4 map up to rounding, in
+    every stage-kernel variant and both precisions; general operators do not fold."""
+    import os
+    d = W.dimer(60)
+    D = d.N * d.N - 1
+    spp, n = 2000, 300
+    outs = {}
+    for flags in (G.GKSL_ASM_FP32, G.GKSL_ASM_FP32 | G.GKSL_ASM_NO_FOLD):
+        ctx = G.dimer_context(d, flags=flags)
+        try:
+            assert G.gksl_get_info(ctx).q1_folded == (0 if flags & G.GKSL_ASM_NO_FOLD else 1)
+            for var in ("0", "1", "2"):
+                os.environ["GKSL_RK4_VARIANT"] = var
+                try:
+                    for prec in (64, 32):
+                        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+                        outs[(flags, var, prec)] = run_gpu(G, ctx, spp, n, n, precision=prec, D=D)[0]
+                finally:
+                    del os.environ["GKSL_RK4_VARIANT"]
+                G.gksl_assemble(ctx, flags)   # a new assembly times/chooses the variant again
+        finally:
+            G.gksl_destroy(ctx)
+    ref = outs[(G.GKSL_ASM_FP32 | G.GKSL_ASM_NO_FOLD, "0", 64)]
+    for (flags, var, prec), v in outs.items():
+        tol = 1e-12 if prec == 64 else 1e-5
+        assert np.abs(v - ref).max() < tol, (flags, var, prec, np.abs(v - ref).max())
+    ctx = G.gksl_create(5)
+    try:
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 1.0, op=W.random_operator(5, 0.6, 3, hermitian=True))
+        G.set_csr_operator(G.gksl_set_h1, ctx, op=W.random_operator(5, 0.6, 4, hermitian=True))
+        G.gksl_set_drive(ctx, 0.5, 0.5, 1.0)
+        G.gksl_assemble(ctx, 0)
+        assert G.gksl_get_info(ctx).q1_folded == 0
+    finally:
+        G.gksl_destroy(ctx)
