@@ -30,7 +30,8 @@ METRIC = "RK4 steps/s & SpMV HBM GB/s at N=1000; Q/K assembly s; batched/adjoint
 UNIT = "RK4 steps/s"
 PROFILE_JSON = os.path.join(ROOT, "profiles", "rk4_stage_fp64_n1000.json")
 # stage-kernel variants of the library (chosen per context by timing)
-KERNEL_OF_VARIANT = {0: "k_stage64<S,18>", 1: "k_stage_pf<S,18,double>", 2: "k_stage_r2<S,18,double>"}
+# stage kernel of each variant; the last template argument is whether Q1 is folded into slot 0
+KERNEL_OF_VARIANT = {0: "k_stage64<S,18,{f}>", 1: "k_stage_pf<S,18,double,{f}>", 2: "k_stage_r2<S,18,double,{f}>"}
 
 
 def dist_env():
@@ -284,7 +285,7 @@ def main():
     hbm, peak_kind = peaks()
     achieved = bytes_launch / (avg_launch_ms * 1e-3) / 1e9
     variant = G.gksl_get_info(ctx).rk4_variant[0]
-    kernel = KERNEL_OF_VARIANT.get(variant, "?")
+    kernel = KERNEL_OF_VARIANT.get(variant, "?").format(f="true" if info.q1_folded else "false")
     traffic = None
     if os.path.exists(PROFILE_JSON):
         pj = json.load(open(PROFILE_JSON))
