@@ -482,7 +482,7 @@ def run_profile_adjoint():
 
 def batched_and_adjoint(G, W, torch):
     """Side measurements: the batched form (256 seeded instances, N in {50, 100, 200}) and the
-    adjoint gradient at N = 200, each against the plain FP64 single-instance path."""
+    adjoint gradient at N = 200 over period 20, each against the plain FP64 single-instance path."""
     out = {}
     inst = W.batch_instances(256, 1812)
     b, ctxs, groups = G.dimer_batch(inst)
@@ -513,19 +513,29 @@ def batched_and_adjoint(G, W, torch):
                       "groups": {str(N): {"instances": n, "steps": s, "instances_per_lane": t[0], "tuned_us": t[1]}
                                  for N, n, s, t in zip(sorted(groups), n_inst, steps, tiles)},
                       "plain_fp64_instance_steps_per_s": inst_steps / plain if plain > 0 else None}
-    # adjoint at N = 200: gradient of the mean of <n1 - n2> over period 1 at the stable step size
+    # adjoint at N = 200: gradient of the mean of <n1 - n2> over period 20 at the stable step
+    # size (the adjoint workload), FP64 and FP32, against a plain FP64 forward pass
     d = W.dimer(200)
     c = G.dimer_context(d)
     try:
         S = G.gksl_min_stable_steps(c)
+        P = 20
+        grads = {}
         for prec in (64, 32):
             grad = np.zeros(4)
             t0 = time.perf_counter()
-            G.gksl_adjoint_timeavg(c, d.obs_diag, S, 1, prec, grad)
+            G.gksl_adjoint_timeavg(c, d.obs_diag, S, P, prec, grad)
             el = time.perf_counter() - t0
-            out[f"adjoint_fp{prec}"] = {"seconds": el, "forward_steps": S, "steps_per_s": S / el}
+            grads[prec] = grad
+            out[f"adjoint_fp{prec}"] = {"seconds": el, "periods": P, "steps_per_period": S, "forward_steps": P * S,
+                                        "steps_per_s": P * S / el, "grad_A_gamma_J_U": list(grad)}
+        out["adjoint_fp32"]["max_rel_diff_vs_fp64"] = float(np.max(np.abs(grads[32] - grads[64]) /
+                                                                   np.abs(grads[64])))
+        G.gksl_propagate(c, S, 64, 64, 0, 0, None)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         G.gksl_propagate(c, S, S, 64, 0, 0, None)
+        torch.cuda.synchronize()
         out["adjoint_plain_fp64_steps_per_s"] = S / (time.perf_counter() - t0)
     finally:
         G.gksl_destroy(c)

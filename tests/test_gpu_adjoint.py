@@ -117,6 +117,66 @@ def test_adjoint_n200_stable_steps_vs_finite_differences(G):
         G.gksl_destroy(ctx)
 
 
+def test_adjoint_workload_period20_vs_finite_differences(G):
+    """The adjoint workload at full size: N = 200 (D = 39 999), loss = mean of <n1 - n2> over
+    period 20 at the stable step count (20 x 13 906 RK4 steps).  The FP64 adjoint's loss equals
+    the forward loss; its gradient with respect to (A, gamma, J, U) matches central differences
+    (h = 1e-6 relative) of that forward loss, computed from every grid point of period 20 emitted
+    to device memory and reduced by the library's observable kernel; the FP32 adjoint stays
+    within 1e-2 of each FP64 component (plus 1e-6 of the largest)."""
+    import torch
+    d = W.dimer(200)
+    P = 20
+    D = d.N * d.N - 1
+    rho0 = d.rho0_dense()
+    ctx = G.dimer_context(d)
+    try:
+        S = G.gksl_min_stable_steps(ctx)
+        grad, grad32 = np.zeros(4), np.zeros(4)
+        L_adj = G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, P, 64, grad)
+        G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, P, 32, grad32)
+        dev = torch.device("cuda", 0)
+        buf = torch.empty((S + 1) * D, dtype=torch.float64, device=dev)
+        obs = torch.empty(S + 1, dtype=torch.float64, device=dev)
+        wt = np.full(S + 1, 1.0 / S)
+        wt[0] = wt[S] = 0.5 / S
+        wt = torch.as_tensor(wt, device=dev)
+
+        def forward_loss():
+            G.gksl_set_rho0(ctx, rho0.real.copy(), rho0.imag.copy())
+            G.gksl_propagate(ctx, S, (P - 1) * S, 64, 0, 0, None)
+            G.gksl_get_state(ctx, buf[:D])
+            G.gksl_propagate(ctx, S, S, 64, 0, 1, buf[D:])
+            G.gksl_observable_diag(ctx, d.obs_diag, buf, S + 1, obs)
+            torch.cuda.synchronize()
+            return float((wt * obs).sum())
+
+        L0 = forward_loss()
+        assert abs(L0 - L_adj) <= 1e-12 * abs(L0), (L0, L_adj)
+        p = d.params
+        base = dict(A=p["A"], rate=d.rate, J=p["J"], U=p["U"])
+
+        def loss(th):
+            G.gksl_set_drive(ctx, p["E"], th["A"], p["omega"])
+            G.gksl_set_gamma(ctx, 0, th["rate"])
+            G.gksl_set_theta(ctx, 0, th["J"])
+            G.gksl_set_theta(ctx, 1, th["U"])
+            G.gksl_assemble(ctx, G.GKSL_ASM_FP32 | G.GKSL_ASM_TRANSPOSE)
+            return forward_loss()
+
+        gmax = np.abs(grad).max()
+        for i, key in enumerate(["A", "rate", "J", "U"]):
+            hfd = 1e-6 * abs(base[key])
+            tp = dict(base); tp[key] += hfd
+            tm = dict(base); tm[key] -= hfd
+            fd = (loss(tp) - loss(tm)) / (2 * hfd)
+            bound = 1e-6 * gmax + 1e-13 * abs(L0) / hfd
+            assert abs(fd - grad[i]) <= bound, (key, fd, grad[i], bound)
+        assert np.all(np.abs(grad32 - grad) <= 1e-2 * np.abs(grad) + 1e-6 * gmax), (grad32, grad)
+    finally:
+        G.gksl_destroy(ctx)
+
+
 def test_autograd_function(G):
     import torch
     d = W.dimer(5)
