@@ -30,8 +30,10 @@ METRIC = "RK4 steps/s & SpMV HBM GB/s at N=1000; Q/K assembly s; batched/adjoint
 UNIT = "RK4 steps/s"
 PROFILE_JSON = os.path.join(ROOT, "profiles", "rk4_stage_fp64_n1000.json")
 # stage-kernel variants of the library (chosen per context by timing)
-# stage kernel of each variant; the last template argument is whether Q1 is folded into slot 0
-KERNEL_OF_VARIANT = {0: "k_stage64<S,18,{f}>", 1: "k_stage_pf<S,18,double,{f}>", 2: "k_stage_r2<S,18,double,{f}>"}
+# stage kernel of each variant ({f}: whether Q1 is folded into slot 0); variant 3 is launched
+# with programmatic dependent launch
+KERNEL_OF_VARIANT = {0: "k_stage64<S,18,{f}>", 1: "k_stage_pf<S,18,double,{f}>",
+                     2: "k_stage_r2<S,18,double,{f}>", 3: "k_stage_pdl<S,18,double,{f}>"}
 
 
 def dist_env():

@@ -279,7 +279,7 @@ typedef struct {
     double assemble_seconds;
     double max_abs_q0;
     int rk4_variant[2];           /* stage-kernel variant in use, [0]: FP64, [1]: FP32 (chosen by timing) */
-    double rk4_variant_us[2][3];  /* timed cost per RK4 step of each variant, microseconds (0: not timed) */
+    double rk4_variant_us[2][4];  /* timed cost per RK4 step of each variant, microseconds (0: not timed) */
     int q1_folded;                /* 1: Q1 folded into the propagation format (see GKSL_ASM_NO_FOLD) */
 } gksl_info;
 

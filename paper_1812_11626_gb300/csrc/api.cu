@@ -662,7 +662,7 @@ extern "C" gksl_status gksl_get_info(gksl_ctx *c, gksl_info *out) {
         out->q1_folded = c->q1_folded ? 1 : 0;
         for (int p = 0; p < 2; ++p) {
             out->rk4_variant[p] = c->rk4_var[p];
-            for (int v = 0; v < 3; ++v) out->rk4_variant_us[p][v] = c->rk4_var_us[p][v];
+            for (int v = 0; v < 4; ++v) out->rk4_variant_us[p][v] = c->rk4_var_us[p][v];
         }
     });
 }

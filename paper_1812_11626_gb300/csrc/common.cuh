@@ -229,7 +229,7 @@ struct gksl_ctx {
     // stage-kernel variant per precision (index 0: FP64, 1: FP32), chosen by timing
     int rk4_var[2] = {0, 0};
     bool rk4_tuned[2] = {false, false};
-    double rk4_var_us[2][3] = {};
+    double rk4_var_us[2][4] = {};
     // cached CUDA graphs for chunks of steps
     struct Graph {
         long long steps = 0;

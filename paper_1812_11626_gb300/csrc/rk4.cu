@@ -207,6 +207,55 @@ __global__ void __launch_bounds__(kThreads, 3) k_stage_pf(HybView<VT> A0, HybVie
     epi<STAGE, VT>(r, s0, v, v64, yn, acc, a.hc);
 }
 
+// Variant 3: variant 1 with programmatic dependent launch.  Each block lets the next stage's
+// launch begin as soon as it starts, loads its rows' matrix columns and values (no stage writes
+// them), and only then waits for the previous stage to complete (griddepcontrol.wait) before it
+// reads the drive table, the step base or a state vector, or writes anything.  The next stage's
+// blocks thus take the SMs the previous stage frees in its last wave and stream their matrix
+// slots meanwhile.
+template <int STAGE, int W, typename VT, bool M>
+__global__ void __launch_bounds__(kThreads, 3) k_stage_pdl(HybView<VT> A0, HybView<VT> A1, StepArgs a,
+                                                           const VT *__restrict__ y, VT *v, double *v64,
+                                                           VT *__restrict__ yn, VT *__restrict__ acc) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if ((int)blockIdx.x < a.nb_long) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        const VT eps = (VT)a.eps_tab[3 * (*a.base + a.local) + eps_slot<STAGE>()];
+        const int lane = threadIdx.x & 31;
+        const long long i = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+        if (i < a.n_long) {
+            VT s0 = tail_dot<VT, VT>(A0, i, lane, y);
+            VT s1 = tail_dot<VT, VT>(A1, i, lane, y);
+            if (lane == 0) epi<STAGE, VT>(a.long_rows[i], s0 + eps * s1, v, v64, yn, acc, a.hc);
+        }
+        return;
+    }
+    const long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
+    const bool in = r < a.D;
+    int c[W];
+    VT m[W];
+    VT q = VT(0);
+    if (in) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) c[j] = ldcs(A0.ell_col + (long long)j * A0.ld + r);
+#pragma unroll
+        for (int j = 0; j < W; ++j) m[j] = ldcs(A0.ell_val + (long long)j * A0.ld + r);
+        if (M) q = ldcs(q1_of<VT>(a) + r);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (!in || c[0] < 0) return;   // past the end, or a long row (handled by a warp above)
+    const VT eps = (VT)a.eps_tab[3 * (*a.base + a.local) + eps_slot<STAGE>()];
+    if (M) m[0] = eps * q + m[0];
+    VT x[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) x[j] = __ldg(y + c[j]);
+    VT s0 = m[0] * x[0];
+#pragma unroll
+    for (int j = 1; j < W; ++j) s0 += m[j] * x[j];
+    if (!M) s0 = s0 + eps * ell_dot_full<VT, VT>(A1, r, y);
+    epi<STAGE, VT>(r, s0, v, v64, yn, acc, a.hc);
+}
+
 // Variant 2: two consecutive rows per thread with 2-wide vector loads of the slot-major ELL
 // arrays (ld is a multiple of 32 and r is even, so every vector access is aligned).
 template <int STAGE, int W, typename VT, bool M>
@@ -305,6 +354,22 @@ Launch make_launch(gksl_ctx *c, const Hyb<double> &h0, double h, const double *t
 
 // One RK4 step; the stage inputs go to y2, y3, y4 (y4 may alias y2: the default buffers are
 // yA, yB, yA).
+// launch with programmatic stream serialization (the kernel waits on its predecessor itself)
+template <typename... P, typename... A>
+void launch_pdl(void (*kernel)(P...), unsigned grid, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GK_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
+}
+
 template <int W, bool M>
 void step64_w(gksl_ctx *c, const Launch &L, double *y2, double *y3, double *y4) {
     auto A0 = view(c->hyb0), A1 = view(c->hyb1);
@@ -325,7 +390,7 @@ void step32_w(gksl_ctx *c, const Launch &L, float *y2, float *y3, float *y4) {
     k_stage32<4, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v32.p, c->v.p, nullptr, c->acc32.p);
 }
 
-// variants 1 and 2 on either precision
+// variants 1, 2 and 3 on either precision
 template <int VAR, int W, typename VT, bool M>
 void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h1, VT *v, double *v64, VT *y2, VT *y3,
               VT *y4, VT *acc) {
@@ -333,7 +398,12 @@ void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h
     cudaStream_t s = c->stream;
     Launch L = L0;
     if (VAR == 2) L.grid = (unsigned)(L.a.nb_long + (c->D + 2 * kThreads - 1) / (2 * kThreads));
-    if constexpr (VAR == 1) {
+    if constexpr (VAR == 3) {
+        launch_pdl(k_stage_pdl<1, W, VT, M>, L.grid, s, A0, A1, L.a, (const VT *)v, v, v64, y2, acc);
+        launch_pdl(k_stage_pdl<2, W, VT, M>, L.grid, s, A0, A1, L.a, (const VT *)y2, v, v64, y3, acc);
+        launch_pdl(k_stage_pdl<3, W, VT, M>, L.grid, s, A0, A1, L.a, (const VT *)y3, v, v64, y4, acc);
+        launch_pdl(k_stage_pdl<4, W, VT, M>, L.grid, s, A0, A1, L.a, (const VT *)y4, v, v64, (VT *)nullptr, acc);
+    } else if constexpr (VAR == 1) {
         k_stage_pf<1, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
         k_stage_pf<2, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
         k_stage_pf<3, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, v, v64, y4, acc);
@@ -353,10 +423,11 @@ void launch_step_csr_t(gksl_ctx *c, int precision, double h, const double *tab, 
     Launch L = make_launch(c, c->hyb0, h, tab, local);
     int W = c->hyb0.width;
     int var = c->rk4_var[precision == 64 ? 0 : 1];
-    if (var == 1 && W != 18) var = 0;   // the register-prefetch variant exists for the 18-slot layout only
+    if ((var == 1 || var == 3) && W != 18) var = 0;   // the register-prefetch variants exist for 18 slots only
     if (precision == 64) {
         double *y2 = Y2 ? (double *)Y2 : c->yA.p, *y3 = Y3 ? (double *)Y3 : c->yB.p, *y4 = Y4 ? (double *)Y4 : c->yA.p;
-        if (var == 1) step_var<1, 18, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
+        if (var == 3) step_var<3, 18, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
+        else if (var == 1) step_var<1, 18, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
         else if (var == 2 && W == 18)
             step_var<2, 18, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
         else if (var == 2) step_var<2, 0, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
@@ -364,7 +435,8 @@ void launch_step_csr_t(gksl_ctx *c, int precision, double h, const double *tab, 
         else step64_w<0, M>(c, L, y2, y3, y4);
     } else {
         float *y2 = Y2 ? (float *)Y2 : c->yA32.p, *y3 = Y3 ? (float *)Y3 : c->yB32.p, *y4 = Y4 ? (float *)Y4 : c->yA32.p;
-        if (var == 1) step_var<1, 18, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
+        if (var == 3) step_var<3, 18, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
+        else if (var == 1) step_var<1, 18, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
         else if (var == 2 && W == 18)
             step_var<2, 18, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
         else if (var == 2)
@@ -389,21 +461,25 @@ void launch_step(gksl_ctx *c, int precision, double h, const double *tab, long l
     launch_step_csr(c, precision, h, tab, local, nullptr, nullptr, nullptr);
 }
 
-// Time the stage-kernel variants on this context's matrix (a few steps each, from a saved
-// copy of the state, which is restored afterwards) and keep the fastest.  Small systems are
-// launch-latency bound and keep variant 0.  GKSL_RK4_VARIANT=0|1|2 forces a variant.
+cudaGraphExec_t graph_for(gksl_ctx *c, long long steps, int precision, double h, const double *tab);
+
+// Time the stage-kernel variants on this context's matrix, each as a CUDA graph of 8 steps as
+// propagation replays them (from a saved copy of the state, which is restored afterwards), and
+// keep the fastest (best of two timed replays).  Systems below D = 1024 keep variant 0.
+// GKSL_RK4_VARIANT=0..3 forces a variant.
 void tune_variant(gksl_ctx *c, int precision, double h, const double *tab) {
+    constexpr int kSteps = 8;
     int pi = precision == 64 ? 0 : 1;
     if (c->rk4_tuned[pi]) return;
     c->rk4_tuned[pi] = true;
     if (c->asm_flags & GKSL_ASM_MATRIX_FREE) return;   // one matrix-free kernel per stage
     const char *env = getenv("GKSL_RK4_VARIANT");
-    if (env && env[0] >= '0' && env[0] <= '2') {
+    if (env && env[0] >= '0' && env[0] <= '3') {
         c->rk4_var[pi] = env[0] - '0';
         return;
     }
     c->rk4_var[pi] = 0;
-    if (c->D < 65536) return;
+    if (c->D < 1024) return;
     long long D1 = c->D + 1;
     DBuf<double> save((size_t)D1);
     GK_CUDA(cudaMemcpyAsync(save.p, c->v.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, c->stream));
@@ -412,17 +488,27 @@ void tune_variant(gksl_ctx *c, int precision, double h, const double *tab) {
     GK_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_v = 0;
-    for (int var = 0; var < 3; ++var) {
+    for (int var = 0; var < 4; ++var) {
+        c->rk4_var_us[pi][var] = 0.0;
+        if ((var == 1 || var == 3) && c->hyb0.width != 18) continue;   // 18-slot layouts only
         c->rk4_var[pi] = var;
+        cudaGraphExec_t g = graph_for(c, kSteps, precision, h, tab);
         k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, 0);
-        for (int i = 0; i < 2; ++i) launch_step(c, precision, h, tab, i);
-        GK_CUDA(cudaEventRecord(e0, c->stream));
-        for (int i = 2; i < 8; ++i) launch_step(c, precision, h, tab, i);
-        GK_CUDA(cudaEventRecord(e1, c->stream));
-        GK_CUDA(cudaEventSynchronize(e1));
-        float ms = 0;
-        GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        c->rk4_var_us[pi][var] = 1000.0 * ms / 6.0;
+        GK_LAUNCH_CHECK();
+        GK_CUDA(cudaGraphLaunch(g, c->stream));   // warm-up
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, 0);
+            GK_LAUNCH_CHECK();
+            GK_CUDA(cudaEventRecord(e0, c->stream));
+            GK_CUDA(cudaGraphLaunch(g, c->stream));
+            GK_CUDA(cudaEventRecord(e1, c->stream));
+            GK_CUDA(cudaEventSynchronize(e1));
+            float t = 0;
+            GK_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            ms = std::min(ms, t);
+        }
+        c->rk4_var_us[pi][var] = 1000.0 * ms / kSteps;
         if (ms < best) { best = ms; best_v = var; }
     }
     cudaEventDestroy(e0);

@@ -41,7 +41,7 @@ class gksl_info(ctypes.Structure):
                 ("ell_width_q0", ctypes.c_int), ("ell_width_q1", ctypes.c_int), ("long_rows", ctypes.c_longlong),
                 ("device_bytes", ctypes.c_longlong), ("assemble_seconds", ctypes.c_double),
                 ("max_abs_q0", ctypes.c_double), ("rk4_variant", ctypes.c_int * 2),
-                ("rk4_variant_us", (ctypes.c_double * 3) * 2), ("q1_folded", ctypes.c_int)]
+                ("rk4_variant_us", (ctypes.c_double * 4) * 2), ("q1_folded", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -201,7 +201,7 @@ def test_min_stable_steps_and_divergence_guard(G):
         G.gksl_destroy(ctx)
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3"])
 def test_stage_kernel_variants(G, variant, monkeypatch):
     """Every stage-kernel variant (forced; normally chosen by timing) on a system large enough
     to be tuned (N = 300, D = 89 999), FP64 against the oracle and FP32 within its tolerance."""
@@ -328,7 +328,7 @@ def test_folded_q1_matches_separate_stream(G):
         ctx = G.dimer_context(d, flags=flags)
         try:
             assert G.gksl_get_info(ctx).q1_folded == (0 if flags & G.GKSL_ASM_NO_FOLD else 1)
-            for var in ("0", "1", "2"):
+            for var in ("0", "1", "2", "3"):
                 os.environ["GKSL_RK4_VARIANT"] = var
                 try:
                     for prec in (64, 32):
