@@ -191,10 +191,14 @@ def cpu_baseline_sample():
     spp = stable_spp_estimate(d)
     h = 2 * np.pi / p["omega"] / spp
     v = SYS.initial_v(d)
-    n = 40
+    # a bounded sample of about 10 s of CPU work: RK4 steps until 10 s have passed (at least 16)
+    n, el = 0, 0.0
+    eps = OP.eps_fn(p["E"], p["A"], p["omega"])
     t0 = time.perf_counter()
-    OP.rk4(Q0, u.Q1, d.rate * u.K1, OP.eps_fn(p["E"], p["A"], p["omega"]), v, h, n)
-    el = time.perf_counter() - t0
+    while n < 16 or el < 10.0:
+        v, _ = OP.rk4(Q0, u.Q1, d.rate * u.K1, eps, v, h, 8, t0=n * h)
+        n += 8
+        el = time.perf_counter() - t0
     return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} FP64 RK4 steps of the N=1000 dimer (scipy CSR SpMV, one thread), "
                       f"after the oracle's definition-route assembly ({asm_s:.1f} s)",

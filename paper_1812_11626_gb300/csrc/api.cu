@@ -467,6 +467,7 @@ extern "C" gksl_status gksl_structure_enumerate(int N, int which, long long capa
 
 extern "C" gksl_status gksl_assemble(gksl_ctx *c, unsigned flags, double *seconds) {
     return guarded(c, [&] {
+        NvtxRange r("gksl_assemble");
         assemble(c, flags);
         if (seconds) *seconds = c->assemble_seconds;
     });
@@ -581,6 +582,7 @@ extern "C" gksl_status gksl_min_stable_steps(gksl_ctx *c, long long *spp) {
 extern "C" gksl_status gksl_propagate(gksl_ctx *c, long long spp, long long n_steps, int precision,
                                       long long correction_every, long long emit_every, double *v_out) {
     return guarded(c, [&] {
+        NvtxRange r("gksl_propagate");
         bool dev = is_device_ptr(v_out);
         propagate(c, spp, n_steps, precision, correction_every, emit_every, v_out, dev);
     });
@@ -623,6 +625,7 @@ extern "C" gksl_status gksl_rho(gksl_ctx *c, const double *v, double *re, double
 extern "C" gksl_status gksl_adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long spp, long long period,
                                             int precision, double *loss, double *grad, int n_grad) {
     return guarded(c, [&] {
+        NvtxRange r("gksl_adjoint_timeavg");
         GK_REQUIRE(o_diag && loss && (grad || n_grad == 0), GKSL_ERR_ARG, "null argument");
         GK_REQUIRE(spp > 0 && period >= 1, GKSL_ERR_ARG, "steps_per_period > 0 and period_index >= 1 required");
         DBuf<double> o((size_t)c->N);

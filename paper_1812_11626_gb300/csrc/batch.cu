@@ -702,6 +702,7 @@ extern "C" gksl_status gksl_batch_reset(gksl_batch *b) {
 extern "C" gksl_status gksl_batch_propagate(gksl_batch *b, const long long *spp, const long long *n_steps,
                                             long long correction_every, double *seconds) {
     return bguarded(b, [&] {
+        NvtxRange r("gksl_batch_propagate");
         GK_REQUIRE(spp && n_steps, GKSL_ERR_ARG, "steps_per_period and n_steps arrays required");
         if (!b->tuned) autotune(b);
         long long maxsteps = 0;

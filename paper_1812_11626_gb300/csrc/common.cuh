@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -33,6 +34,15 @@ struct Error {
     } while (0)
 
 #define GK_LAUNCH_CHECK() GK_CUDA(cudaGetLastError())
+
+// NVTX range over a library call (header-only NVTX3: inert unless a profiler or tracer is
+// attached), so timelines and ncu --nvtx filters see assembly, propagation and gradients
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ------------------------------------------------------------------ device buffers
 
