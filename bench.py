@@ -334,6 +334,15 @@ def main():
         b32 = stage_bytes(info.nnz_q0, info.nnz_q1, D, 32, bool(info.q1_folded))
         extras["fp32_bulk"] = {"value": args.steps * STEP_RK4 / (ms32 * 1e-3), "unit": UNIT,
                                "achieved_gbs": b32 / (ms32 * 1e-3 / (args.steps * STEP_RK4 * 4)) / 1e9}
+        # its error against the FP64 path after STEP_RK4 steps from rho0
+        v32, v64 = np.zeros((1, D)), np.zeros((1, D))
+        for prec, dst in ((32, v32), (64, v64)):
+            G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+            G.gksl_propagate(ctx, spp, STEP_RK4, prec, 0, STEP_RK4, dst)
+        o = np.zeros(2)
+        G.gksl_observable_diag(ctx, d.obs_diag, np.concatenate([v32, v64]), 2, o)
+        extras["fp32_bulk"].update({"steps_compared": STEP_RK4, "max_abs_dv_vs_fp64": float(np.abs(v32 - v64).max()),
+                                    "obs_n1_minus_n2_diff_vs_fp64": float(abs(o[0] - o[1]))})
         extras["assembly_s"] = asm_s
         extras["nnz_q0"] = info.nnz_q0
         extras["device_bytes"] = info.device_bytes
@@ -403,6 +412,12 @@ def matrix_free_extras(G, W, torch, stream, d, spp, steps):
     G.gksl_propagate(ctx, spp, STEP_RK4, 64, 0, STEP_RK4, va)
     G.gksl_propagate(ref, spp, STEP_RK4, 64, 0, STEP_RK4, vb)
     out["max_abs_diff_vs_csr_fp64"] = float(np.abs(va - vb).max())
+    G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+    G.gksl_propagate(ctx, spp, STEP_RK4, 32, 0, STEP_RK4, va)
+    o = np.zeros(2)
+    G.gksl_observable_diag(ref, d.obs_diag, np.concatenate([va, vb]), 2, o)
+    out["fp32"]["max_abs_dv_vs_csr_fp64"] = float(np.abs(va - vb).max())
+    out["fp32"]["obs_n1_minus_n2_diff_vs_csr_fp64"] = float(abs(o[0] - o[1]))
     G.gksl_destroy(ref)
     G.gksl_destroy(ctx)
     return out
@@ -502,6 +517,24 @@ def batched_and_adjoint(G, W, torch):
     sec = G.gksl_batch_propagate(b, spps, steps, 0)
     inst_steps = sum(n * s for n, s in zip(n_inst, steps))
     tiles = [G.gksl_batch_info(b, i) for i in range(len(ctxs))]
+    # error of the batched form (FP32 bulk, FP64 master) against the plain FP64 path: the first
+    # instance of every group after the same steps, from the same state
+    errors, first = [], 0
+    for (N, idx), spp_g, s in zip(sorted(groups.items()), spps, steps):
+        x = inst[idx[0]]
+        D_g = N * N - 1
+        vb = np.zeros(D_g)
+        G.gksl_batch_get_state(b, first, vb)
+        d1 = W.dimer(N, dict(A=x["A"], gamma=x["gamma"]))
+        c1 = G.dimer_context(d1, flags=0)
+        vp = np.zeros((1, D_g))
+        G.gksl_propagate(c1, spp_g, s, 64, 0, s, vp)
+        o = np.zeros(2)
+        G.gksl_observable_diag(c1, d1.obs_diag, np.stack([vb, vp[0]]), 2, o)
+        errors.append({"N": N, "instance": first, "steps": s, "max_abs_dv": float(np.abs(vb - vp[0]).max()),
+                       "obs_n1_minus_n2_diff": float(abs(o[0] - o[1]))})
+        G.gksl_destroy(c1)
+        first += len(idx)
     G.gksl_batch_destroy(b)
     # plain FP64 single-instance path on the same groups for comparison
     plain = 0.0   # seconds the plain path needs for the same instance-steps, run one by one
@@ -518,7 +551,8 @@ def batched_and_adjoint(G, W, torch):
     out["batched"] = {"instance_steps_per_s": inst_steps / sec, "instances": sum(n_inst),
                       "groups": {str(N): {"instances": n, "steps": s, "instances_per_lane": t[0], "tuned_us": t[1]}
                                  for N, n, s, t in zip(sorted(groups), n_inst, steps, tiles)},
-                      "plain_fp64_instance_steps_per_s": inst_steps / plain if plain > 0 else None}
+                      "plain_fp64_instance_steps_per_s": inst_steps / plain if plain > 0 else None,
+                      "error_vs_plain_fp64": errors}
     # adjoint at N = 200: gradient of the mean of <n1 - n2> over period 20 at the stable step
     # size (the adjoint workload), FP64 and FP32, against a plain FP64 forward pass
     d = W.dimer(200)
