@@ -68,7 +68,8 @@ class CSR:
         return sp.csr_matrix((self.re + 1j * self.im, self.col, self.rowptr), shape=(self.n, self.n))
 
 
-BASELINE = dict(J=1.0, U=0.5, E=1.0, A=1.5, omega=1.0, gamma=0.1)
+# parameters of the driven dimer workloads (rate gamma / M on the jump operator)
+DIMER_PARAMS = dict(J=1.0, U=0.5, E=1.0, A=1.5, omega=1.0, gamma=0.1)
 
 
 def _hop(n, M):
@@ -96,7 +97,7 @@ class Dimer:
 
 def dimer(N, params=None, paper_variant=False):
     """Operators of the driven Bose dimer with N Fock states (M = N - 1 bosons)."""
-    p = dict(BASELINE)
+    p = dict(DIMER_PARAMS)
     if params:
         p.update(params)
     M = N - 1
