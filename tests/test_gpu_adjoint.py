@@ -33,7 +33,7 @@ def oracle_grad(d, S, period):
 
 
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 2e-3)])
-def test_adjoint_vs_oracle(G, precision, tol):
+def test_adjoint_vs_oracle(G, precision, tol, record):
     d = W.dimer(6)
     S, period = 60, 3
     ctx = G.dimer_context(d)
@@ -41,8 +41,10 @@ def test_adjoint_vs_oracle(G, precision, tol):
         grad = np.zeros(4)   # [A, rate (gamma_0), J (theta_0), U (theta_1)]
         loss = G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, period, precision, grad)
         L, g = oracle_grad(d, S, period)
+        record("loss_abs_diff_vs_oracle", abs(loss - L))
         assert abs(loss - L) < (1e-11 if precision == 64 else 1e-4)
         scale = np.abs(g).max()
+        record("grad_max_abs_diff_vs_oracle_over_max", np.abs(grad - g).max() / scale)
         assert np.abs(grad - g).max() < tol * scale, (grad, g)
         # the state is left unchanged
         v = np.zeros(d.N * d.N - 1)
@@ -117,7 +119,7 @@ def test_adjoint_n200_stable_steps_vs_finite_differences(G):
         G.gksl_destroy(ctx)
 
 
-def test_adjoint_workload_period20_vs_finite_differences(G):
+def test_adjoint_workload_period20_vs_finite_differences(G, record):
     """The adjoint workload at full size: N = 200 (D = 39 999), loss = mean of <n1 - n2> over
     period 20 at the stable step count (20 x 13 906 RK4 steps).  The FP64 adjoint's loss equals
     the forward loss; its gradient with respect to (A, gamma, J, U) matches central differences
@@ -152,6 +154,7 @@ def test_adjoint_workload_period20_vs_finite_differences(G):
             return float((wt * obs).sum())
 
         L0 = forward_loss()
+        record("loss_rel_diff_adjoint_vs_forward", abs(L0 - L_adj) / abs(L0))
         assert abs(L0 - L_adj) <= 1e-12 * abs(L0), (L0, L_adj)
         p = d.params
         base = dict(A=p["A"], rate=d.rate, J=p["J"], U=p["U"])
@@ -171,7 +174,9 @@ def test_adjoint_workload_period20_vs_finite_differences(G):
             tm = dict(base); tm[key] -= hfd
             fd = (loss(tp) - loss(tm)) / (2 * hfd)
             bound = 1e-6 * gmax + 1e-13 * abs(L0) / hfd
+            record(f"grad_{key}_rel_diff_vs_central_differences", abs(fd - grad[i]) / abs(grad[i]))
             assert abs(fd - grad[i]) <= bound, (key, fd, grad[i], bound)
+        record("fp32_grad_max_rel_diff_vs_fp64", np.max(np.abs(grad32 - grad) / np.abs(grad)))
         assert np.all(np.abs(grad32 - grad) <= 1e-2 * np.abs(grad) + 1e-6 * gmax), (grad32, grad)
     finally:
         G.gksl_destroy(ctx)

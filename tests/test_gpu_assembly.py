@@ -144,7 +144,7 @@ def test_assembly_dimer_vs_oracle(G, N):
         G.gksl_destroy(ctx)
 
 
-def test_assembly_dimer_n1000_full(G):
+def test_assembly_dimer_n1000_full(G, record):
     """Largest configuration: every entry of Q0, Q1, K at N = 1000 (D = 999999) against the oracle."""
     N = 1000
     d = W.dimer(N)
@@ -155,11 +155,14 @@ def test_assembly_dimer_n1000_full(G):
         Q0r = u.q0(p["J"], p["U"], d.rate)
         scale = abs(Q0r).max()
         Q0 = csr_of(G, ctx, G.GKSL_MAT_Q0)
+        record("q0_max_abs_err_over_max_q0", abs(Q0 - Q0r).max() / scale)
         assert abs(Q0 - Q0r).max() <= TOL_ASM * scale
         Q1 = csr_of(G, ctx, G.GKSL_MAT_Q1)
+        record("q1_max_abs_err_over_max_q1", abs(Q1 - u.Q1).max() / abs(u.Q1).max())
         assert abs(Q1 - u.Q1).max() <= TOL_ASM * abs(u.Q1).max()
         K = np.zeros(N * N - 1)
         G.gksl_get_k(ctx, K)
+        record("k_max_abs_err_over_max_q0", np.abs(K - d.rate * u.K1).max() / scale)
         assert np.abs(K - d.rate * u.K1).max() <= TOL_ASM * scale
         info = G.gksl_get_info(ctx)
         # propagation matrix Q0 + E Q1 after the 64 eps max|Q| drop has 18 448 539 entries (oracle,
@@ -168,6 +171,8 @@ def test_assembly_dimer_n1000_full(G):
         Qe.data[np.abs(Qe.data) <= 64 * np.finfo(float).eps * abs(Qe).max()] = 0
         Qe.eliminate_zeros()
         nk = int((np.abs(d.rate * u.K1) > 64 * np.finfo(float).eps * abs(Qe).max()).sum())
+        record("nnz_q0_gpu", info.nnz_q0)
+        record("nnz_q0_oracle", Qe.nnz + nk)
         assert abs(info.nnz_q0 - (Qe.nnz + nk)) <= 10, (info.nnz_q0, Qe.nnz, nk)
         assert info.ell_width_q0 == 18
     finally:

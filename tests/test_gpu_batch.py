@@ -50,7 +50,7 @@ def test_batch_mixed_n_vs_oracle(G):
             G.gksl_destroy(c)
 
 
-def test_batch_256_seeded_instances_sampled(G):
+def test_batch_256_seeded_instances_sampled(G, record):
     """The batched workload at full size (256 seeded instances, N in {50, 100, 200}) in the launch
     configuration the benchmark times: a tenth of a period per group at its stable step size;
     three instances of every group against their own oracle runs (FP32 bulk tolerance)."""
@@ -60,7 +60,7 @@ def test_batch_256_seeded_instances_sampled(G):
         spps = [spp for _, _, spp in groups]
         steps = [max(1, s // 10) for s in spps]
         G.gksl_batch_propagate(b, spps, steps, 0)
-        pos = 0
+        pos, worst = 0, 0.0
         for (N, idx, spp), n in zip(groups, steps):
             for j in (0, len(idx) // 2, len(idx) - 1):
                 x = inst[idx[j]]
@@ -69,8 +69,10 @@ def test_batch_256_seeded_instances_sampled(G):
                 v_ref, _ = SYS.propagate_dimer(d, u, spp, n)
                 v = np.zeros(N * N - 1)
                 G.gksl_batch_get_state(b, pos + j, v)
+                worst = max(worst, np.abs(v - v_ref).max())
                 assert np.abs(v - v_ref).max() < 1e-5, (N, j, np.abs(v - v_ref).max())
             pos += len(idx)
+        record("max_abs_dv_vs_oracle_9_sampled_instances", worst)
     finally:
         G.gksl_batch_destroy(b)
         for c in ctxs:

@@ -32,7 +32,7 @@ def run_gpu(G, ctx, spp, nsteps, emit, precision=64, corr=0, D=None):
     return out
 
 
-def test_config0_fp64_n10(G):
+def test_config0_fp64_n10(G, record):
     """N = 10 dimer, 10 periods x 200 steps, v at every period end (the small workload)."""
     d = W.dimer(10)
     ctx = G.dimer_context(d)
@@ -41,12 +41,16 @@ def test_config0_fp64_n10(G):
         u = SYS.unfold_dimer(d)
         _, ref = SYS.propagate_dimer(d, u, 200, 2000, emit_every=200)
         err = max(np.abs(out[i] - ref[i]).max() for i in range(10))
+        record("fp64_max_abs_dv_vs_oracle", err)
         assert err < TOL64, err
         w, c0 = OP.observable_weights(d.obs_diag)
         obs = np.zeros(10)
         G.gksl_observable_diag(ctx, d.obs_diag, out, 10, obs)
+        record("obs_max_abs_diff_vs_oracle", np.abs(obs - np.array([c0 + w @ r for r in ref])).max())
         assert np.abs(obs - np.array([c0 + w @ r for r in ref])).max() < 1e-9
         rho = OB.rho_from_v(out[-1], N=10)
+        record("rho_trace_minus_1", abs(np.trace(rho) - 1))
+        record("rho_min_eigenvalue", np.linalg.eigvalsh(rho).min())
         assert abs(np.trace(rho) - 1) < 1e-14 and np.linalg.eigvalsh(rho).min() > -1e-8
     finally:
         G.gksl_destroy(ctx)
@@ -84,7 +88,7 @@ def test_random_operators_fp64(G):
         G.gksl_destroy(ctx)
 
 
-def test_config1_n100_fp64_and_fp32(G):
+def test_config1_n100_fp64_and_fp32(G, record):
     """N = 100 (D = 9999) at the stable 4000 steps/period: FP64 parity over a quarter period,
     FP32 bulk error against FP64 over two periods."""
     d = W.dimer(100)
@@ -95,6 +99,7 @@ def test_config1_n100_fp64_and_fp32(G):
         out = run_gpu(G, ctx, spp, 1000, 500, D=D)
         u = SYS.unfold_dimer(d)
         _, ref = SYS.propagate_dimer(d, u, spp, 1000, emit_every=500)
+        record("fp64_max_abs_dv_vs_oracle", max(np.abs(out[i] - ref[i]).max() for i in range(2)))
         assert max(np.abs(out[i] - ref[i]).max() for i in range(2)) < TOL64
         # FP32 bulk vs FP64, both on the GPU, from rho0
         G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
@@ -110,7 +115,7 @@ def test_config1_n100_fp64_and_fp32(G):
         G.gksl_destroy(ctx)
 
 
-def test_config1_full_length_fp32_vs_fp64(G):
+def test_config1_full_length_fp32_vs_fp64(G, record):
     """N = 100 over the full 100 periods at the stable 4000 steps/period (400 000 steps): the FP32
     bulk form with an FP64 step every period against the FP64 path, on v and <n1 - n2> at every
     tenth period end."""
@@ -122,10 +127,12 @@ def test_config1_full_length_fp32_vs_fp64(G):
         v64 = run_gpu(G, ctx, spp, spp * periods, spp * 10, D=D)
         G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
         v32 = run_gpu(G, ctx, spp, spp * periods, spp * 10, precision=32, corr=spp, D=D)
+        record("fp32_max_abs_dv_vs_fp64", np.abs(v32 - v64).max())
         assert np.abs(v32 - v64).max() < TOL32_V
         o64, o32 = np.zeros(10), np.zeros(10)
         G.gksl_observable_diag(ctx, d.obs_diag, v64, 10, o64)
         G.gksl_observable_diag(ctx, d.obs_diag, v32, 10, o32)
+        record("fp32_obs_max_abs_diff_vs_fp64", np.abs(o32 - o64).max())
         assert np.abs(o32 - o64).max() < TOL32_O
     finally:
         G.gksl_destroy(ctx)
@@ -226,7 +233,7 @@ def test_stage_kernel_variants(G, variant, monkeypatch):
         G.gksl_destroy(ctx)
 
 
-def test_config4_n1000_fp64_steps(G):
+def test_config4_n1000_fp64_steps(G, record):
     """Largest workload (N = 1000, D = 999999) in the launch configuration of the benchmark:
     a few FP64 steps at the stable step size against the oracle's RK4 on its own matrices."""
     d = W.dimer(1000)
@@ -238,9 +245,11 @@ def test_config4_n1000_fp64_steps(G):
         out = run_gpu(G, ctx, spp, nst, nst, D=D)
         u = SYS.unfold_dimer(d)
         v_ref, _ = SYS.propagate_dimer(d, u, spp, nst)
+        record("fp64_max_abs_dv_vs_oracle", np.abs(out[0] - v_ref).max())
         assert np.abs(out[0] - v_ref).max() < TOL64
         G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
         o32 = run_gpu(G, ctx, spp, nst, nst, precision=32, corr=0, D=D)
+        record("fp32_max_abs_dv_vs_oracle", np.abs(o32[0] - v_ref).max())
         assert np.abs(o32[0] - v_ref).max() < TOL32_V
     finally:
         G.gksl_destroy(ctx)
