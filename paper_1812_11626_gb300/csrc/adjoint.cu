@@ -14,13 +14,15 @@
 // products u_c . Y_i.  Each stage is one fused kernel; gradient partial sums are kept per
 // block in fixed slots and reduced in a fixed order at the end (deterministic).
 //
-// Schedule: period checkpoints from one forward pass; then, period by period in reverse,
-// checkpoints every q steps (q ~ sqrt(S/4)), and segment by segment in reverse one CUDA graph
+// Schedule: checkpoints every q steps (q ~ sqrt(S/4)) from one forward pass when they fit in
+// memory, else period checkpoints and, period by period in reverse, a forward pass that sets
+// the checkpoints of the period's segments; then segment by segment in reverse one CUDA graph
 // that re-runs the segment's q steps forward, keeping every stage input Y1..Y4 of each step,
 // and then sweeps the same steps backwards.  Every per-step scalar (the drive at the stage
 // times, the loss weight of the step) is read from device tables indexed by the step, so one
-// graph per segment length serves every segment.  Each state is recomputed at most twice;
-// memory is (periods + S/q) state checkpoints plus 4 q stage inputs.
+// graph per segment length serves every segment.  Each state is computed twice (three times
+// without room for every checkpoint); memory is periods * S/q state checkpoints (periods + S/q
+// without room) plus 4 q stage inputs.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -419,10 +421,17 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
     observable_weights(c, o_diag, w.p, c0.p);
     const Basis B(c->N);
 
-    // checkpoints: one per period, one every q steps of the period being reversed
+    // checkpoints every q steps.  When those of all periods fit in a quarter of the free device
+    // memory, the first forward pass keeps them all and no period is run forward a second time
+    // before its stage-input pass; otherwise it keeps one per period and each period, when its
+    // turn comes, is run forward once more to set the checkpoints of its segments.
     const long long q = std::max(1LL, std::min(S, (long long)std::ceil(std::sqrt((double)S / 4.0))));
     const long long nseg = (S + q - 1) / q;
-    DBuf<double> v_save((size_t)D1), ckP((size_t)(period * D1)), seg((size_t)(nseg * D1));
+    size_t free_b = 0, total_b = 0;
+    GK_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const bool keep_all = (double)period * nseg * D1 * sizeof(double) <= 0.25 * (double)free_b;
+    DBuf<double> v_save((size_t)D1), ckP((size_t)((keep_all ? 1 : period) * D1)),
+        seg((size_t)((keep_all ? period : 1) * nseg * D1));
     DBuf<double> lam((size_t)D1), lacc((size_t)D1), obs((size_t)(S + 1));
     DBuf<double> part((size_t)grid * nslot);
     GK_CUDA(cudaMemsetAsync(part.p, 0, sizeof(double) * grid * nslot, s));
@@ -495,27 +504,41 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
         return e;
     };
 
-    // 1. forward pass: period checkpoints (the last period's end state is not needed)
+    // 1. forward pass: the checkpoints of every segment (keep_all) or of every period; the end
+    // state of the last period is not needed
     load_state(v_save.p);
-    for (long long p = 0; p < period; ++p) {
-        save_state(ckP.p + p * D1);
-        if (p + 1 < period) advance(c, precision, h, p * S, S);
+    if (keep_all) {
+        for (long long p = 0; p < period; ++p)
+            for (long long j = 0; j < nseg; ++j) {
+                save_state(seg.p + (p * nseg + j) * D1);
+                if (p + 1 == period && j + 1 == nseg) break;
+                set_step_base(c, p * S + j * q);
+                GK_CUDA(cudaGraphLaunch(segment_graph(std::min(q, S - j * q), 0), s));
+            }
+    } else {
+        for (long long p = 0; p < period; ++p) {
+            save_state(ckP.p + p * D1);
+            if (p + 1 < period) advance(c, precision, h, p * S, S);
+        }
     }
     // 2. reverse sweep; lam starts as dL/dv at the last grid point
     k_fill_scaled<<<grid_for(D1, 256), 256, 0, s>>>(lam.p, w.p, 0.5 / (double)S, D1);
     GK_LAUNCH_CHECK();
     for (long long p = period - 1; p >= 0; --p) {
-        load_state(ckP.p + p * D1);
         const int mode = (p == period - 1) ? 2 : 1;
-        for (long long j = 0; j < nseg; ++j) {
-            save_state(seg.p + j * D1);
-            if (j + 1 == nseg) break;   // the last segment starts from this checkpoint
-            set_step_base(c, p * S + j * q);
-            GK_CUDA(cudaGraphLaunch(segment_graph(q, 0), s));
+        const double *segp = seg.p + (keep_all ? p * nseg * D1 : 0);
+        if (!keep_all) {
+            load_state(ckP.p + p * D1);
+            for (long long j = 0; j < nseg; ++j) {
+                save_state(seg.p + j * D1);
+                if (j + 1 == nseg) break;   // the last segment starts from this checkpoint
+                set_step_base(c, p * S + j * q);
+                GK_CUDA(cudaGraphLaunch(segment_graph(q, 0), s));
+            }
         }
         for (long long j = nseg - 1; j >= 0; --j) {
             const long long len = std::min(q, S - j * q);
-            load_state(seg.p + j * D1);
+            load_state(segp + j * D1);
             set_step_base(c, p * S + j * q);
             GK_CUDA(cudaGraphLaunch(segment_graph(len, mode), s));
         }
