@@ -283,3 +283,72 @@ def test_argument_validation(G):
         assert e.value.status == G.GKSL_ERR_STATE
     finally:
         G.gksl_destroy(ctx)
+
+
+def test_assembly_is_well_formed_and_deterministic(G):
+    """compute-sanitizer is closed on this machine; in its place every assembled matrix is checked
+    for well-formed CSR (monotone row pointers, columns in range, strictly increasing within a
+    row, finite values), and two assemblies of the same operators -- a dimer and general random
+    operators with two channels -- must agree bit for bit (the atomic-based scatter of the radix
+    sort must not leak its ordering into the result), as must two propagations from them."""
+    def mats(ctx):
+        out = {}
+        for which in (G.GKSL_MAT_Q0, G.GKSL_MAT_Q1, G.GKSL_MAT_H0 + 0, G.GKSL_MAT_R + 0):
+            out[which] = G.get_csr_numpy(ctx, which)
+        K = np.zeros(G.gksl_get_info(ctx).D)
+        G.gksl_get_k(ctx, K)
+        out["K"] = K
+        return out
+
+    def check(m, D):
+        for which, val in m.items():
+            if which == "K":
+                assert np.all(np.isfinite(val))
+                continue
+            rp, col, v = val
+            nnz = int(rp[-1])
+            assert rp[0] == 0 and np.all(np.diff(rp) >= 0), which
+            col, v = col[:nnz], v[:nnz]
+            assert np.all((col >= 0) & (col < D)), which
+            for r in range(D):
+                c = col[rp[r]:rp[r + 1]]
+                assert np.all(np.diff(c) > 0), (which, r)
+            assert np.all(np.isfinite(v)), which
+
+    def build_dimer():
+        return G.dimer_context(W.dimer(40))
+
+    def build_random():
+        N = 9
+        ctx = G.gksl_create(N)
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 0.7, op=W.random_operator(N, 0.5, 11, hermitian=True))
+        G.set_csr_operator(G.gksl_set_h1, ctx, op=W.random_operator(N, 0.4, 12, hermitian=True))
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, 0.3, op=W.random_operator(N, 0.5, 13))
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 1, 0.2, op=W.random_operator(N, 0.5, 14))
+        G.gksl_set_drive(ctx, 0.4, 0.6, 1.5)
+        G.gksl_assemble(ctx, G.GKSL_ASM_FP32)
+        rho0 = np.eye(N) / N
+        G.gksl_set_rho0(ctx, rho0)
+        return ctx
+
+    for build in (build_dimer, build_random):
+        runs = []
+        for _ in range(2):
+            ctx = build()
+            try:
+                D = G.gksl_get_info(ctx).D
+                m = mats(ctx)
+                check(m, D)
+                out = np.zeros((1, D))
+                G.gksl_propagate(ctx, 400, 100, 64, 0, 100, out)
+                runs.append((m, out))
+            finally:
+                G.gksl_destroy(ctx)
+        (m1, o1), (m2, o2) = runs
+        for which in m1:
+            if which == "K":
+                assert np.array_equal(m1[which], m2[which])
+            else:
+                for a, b in zip(m1[which], m2[which]):
+                    assert np.array_equal(a, b), which
+        assert np.array_equal(o1, o2)
