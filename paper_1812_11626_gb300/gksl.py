@@ -325,8 +325,11 @@ def gksl_propagate_csr_noalloc(D, a0_rowptr, a0_col, a0_val, a1_rowptr, a1_col, 
     st = _lib.gksl_propagate_csr_noalloc(int(D), _ptr(a0_rowptr), _ptr(a0_col), _ptr(a0_val), _ptr(a1_rowptr),
                                          _ptr(a1_col), _ptr(a1_val), _ptr(K), _ptr(v), float(t0), float(h),
                                          int(n_steps), float(E), float(A), float(omega), cuda_stream)
+    if st == GKSL_ERR_ARG:
+        raise GkslError(st, f"gksl_propagate_csr_noalloc: D = {int(D)} must be in [1, GKSL_NOALLOC_MAX_D = "
+                            f"{GKSL_NOALLOC_MAX_D}], h > 0, n_steps >= 0 and the A0, v pointers non-null")
     if st != GKSL_OK:
-        raise GkslError(st, "gksl_propagate_csr_noalloc failed (argument out of range or CUDA error)")
+        raise GkslError(st, f"gksl_propagate_csr_noalloc failed with status {st} (a CUDA launch failed)")
 
 
 # ------------------------------------------------------------------ conveniences over the calls
