@@ -377,31 +377,46 @@ __global__ void __launch_bounds__(kThreads, BL == 1 ? 3 : 2) k_mf_stage(MfArgs a
 #pragma unroll
     for (int i = 0; i < kRJ; ++i) { X[i].x = T(0); X[i].y = T(0); }
 
-    // row terms: -i H rho - Gamma rho, down the column c
-    {
-        C p[kRJ + 2 * G::BR];
-#pragma unroll
-        for (int t = 0; t < kRJ + 2 * G::BR; ++t) p[t] = rho[(i0 + G::BT - G::BR + t) * G::RW + c + G::BT];
-#pragma unroll
-        for (int i = 0; i < kRJ; ++i) {
-#pragma unroll
-            for (int d = -BH; d <= BH; ++d) row_h<REAL>(X[i], hrow[(i0 + i) * G::WH + d + BH], p[i + G::BR + d]);
-#pragma unroll
-            for (int d = -BG; d <= BG; ++d) row_g<REAL>(X[i], grow[(i0 + i) * G::WG + d + BG], p[i + G::BR + d]);
-        }
-    }
-    // column terms: i rho H - rho Gamma, along the rows of this thread
+    // row terms -i H rho - Gamma rho down the column c, and column terms i rho H - rho Gamma
+    // along the rows of this thread.  The row and column taps at offset 0 act on the same
+    // entry rho_jk, so they are applied once with the merged coefficients
+    // (h_jj - conj(h_kk)) and (g_jj + conj(g_kk)) (as row taps).
     {
         C hc[G::WH], gc[G::WG];
 #pragma unroll
         for (int d = 0; d < G::WH; ++d) hc[d] = hcol[c * G::WH + d];
 #pragma unroll
         for (int d = 0; d < G::WG; ++d) gc[d] = gcol[c * G::WG + d];
+        C p[kRJ + 2 * G::BR];
+#pragma unroll
+        for (int t = 0; t < kRJ + 2 * G::BR; ++t) p[t] = rho[(i0 + G::BT - G::BR + t) * G::RW + c + G::BT];
+#pragma unroll
+        for (int i = 0; i < kRJ; ++i) {
+#pragma unroll
+            for (int d = -BH; d <= BH; ++d) {
+                C h = hrow[(i0 + i) * G::WH + d + BH];
+                if (d == 0) {
+                    h.x -= hc[BH].x;
+                    if (!REAL) h.y += hc[BH].y;
+                }
+                row_h<REAL>(X[i], h, p[i + G::BR + d]);
+            }
+#pragma unroll
+            for (int d = -BG; d <= BG; ++d) {
+                C g = grow[(i0 + i) * G::WG + d + BG];
+                if (d == 0) {
+                    g.x += gc[BG].x;
+                    if (!REAL) g.y -= gc[BG].y;
+                }
+                row_g<REAL>(X[i], g, p[i + G::BR + d]);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < kRJ; ++i) {
             const C *rr = rho + (i0 + i + G::BT) * G::RW + c + G::BT;
 #pragma unroll
             for (int d = -G::BR; d <= G::BR; ++d) {
+                if (d == 0) continue;   // merged into the row taps above
                 const C pv = rr[d];
                 if (d >= -BH && d <= BH) col_h<REAL>(X[i], hc[d + BH], pv);
                 if (d >= -BG && d <= BG) col_g<REAL>(X[i], gc[d + BG], pv);
