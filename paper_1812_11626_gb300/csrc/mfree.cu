@@ -71,6 +71,8 @@ struct MfArgs {
     const long long *base;
     long long local;
     HConst hc;
+    double diag0;   // sqrt(2)/N: the F0/N part of rho on the diagonal image (computed on the host)
+    float diag0f;
 };
 
 // the vectors of one stage: input y, state v (FP64 master v64), next input yn, accumulator, and
@@ -189,7 +191,7 @@ __device__ inline void load_rho(typename Cx<T>::t *rho, const MfArgs &a, const M
     constexpr int IT = (RH + kThreads / 32 - 1) / (kThreads / 32);     // central part, rows per warp
     constexpr int nh = RH * 2 * BT, IH = (nh + kThreads - 1) / kThreads;  // halo columns
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const T diag0 = (T)(M_SQRT2 / (double)a.N);
+    const T diag0 = sizeof(T) == 8 ? (T)a.diag0 : (T)a.diag0f;
     C val[IT], hal[IH];
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
@@ -916,6 +918,8 @@ void mf_step(gksl_ctx *c, int precision, double h, const double *tab, long long 
     a.hc.hf = (float)h;
     a.hc.h2f = 0.5f * (float)h;
     a.hc.h6f = (float)(h / 6.0);
+    a.diag0 = M_SQRT2 / (double)c->N;
+    a.diag0f = (float)a.diag0;
     const unsigned grid = (unsigned)m.n_tiles;
     const bool narrow = m.bh == 1;
     if (precision == 64) {
