@@ -29,11 +29,10 @@ STEP_RK4 = 2000          # RK4 steps per bench step
 METRIC = "RK4 steps/s & SpMV HBM GB/s at N=1000; Q/K assembly s; batched/adjoint vs plain"
 UNIT = "RK4 steps/s"
 PROFILE_JSON = os.path.join(ROOT, "profiles", "rk4_stage_fp64_n1000.json")
-# stage-kernel variants of the library (chosen per context by timing)
-# stage kernel of each variant ({f}: whether Q1 is folded into slot 0); variant 3 is launched
-# with programmatic dependent launch
-KERNEL_OF_VARIANT = {0: "k_stage64<S,18,{f}>", 1: "k_stage_pf<S,18,double,{f}>",
-                     2: "k_stage_r2<S,18,double,{f}>", 3: "k_stage_pdl<S,18,double,{f}>"}
+# stage kernel of each variant of the library (chosen per context by timing; {f}: Q1 folded into
+# slot 0, {c}: 16-bit columns); variant 3 is launched with programmatic dependent launch
+KERNEL_OF_VARIANT = {0: "k_stage64<S,18,{f},{c}>", 1: "k_stage_pf<S,18,double,{f},{c}>",
+                     2: "k_stage_r2<S,18,double,{f}>", 3: "k_stage_pdl<S,18,double,{f},{c}>"}
 
 
 def dist_env():
@@ -97,20 +96,32 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
-def stage_bytes(nnz0, nnz1, D, precision, q1_folded=False):
+def stage_bytes(nnz0, nnz1, D, precision, q1_folded=False, wide_entries=None):
     """Compulsory bytes per RK4 stage launch, averaged over the 4 stages of a step.
 
     Matrix stream: value + int32 column per stored entry of [Q0 + E Q1 | K] (no row pointers in
     the ELL layout) and of Q1; with Q1 folded into the first slot of its row, one Q1 value per
-    row instead.  Vectors, per step: stage 1 reads v once (also the gather source) and writes y2
-    and acc; stages 2-3 gather y, read v, write y_next, read+write acc; stage 4 gathers y4,
-    reads+writes v, reads acc: 17 vector passes of D elements, plus the FP64 master update
-    (read+write) of the FP32 form.
+    row instead.  With 16-bit columns (wide_entries given: the entries still read with int32
+    columns, i.e. the long rows' entries and the slots of the escaped rows), value + 2 bytes
+    per entry and 2 more per wide entry.  Vectors, per step: stage 1 reads v once (also the
+    gather source) and writes y2 and acc; stages 2-3 gather y, read v, write y_next, read+write
+    acc; stage 4 gathers y4, reads+writes v, reads acc: 17 vector passes of D elements, plus the
+    FP64 master update (read+write) of the FP32 form.
     """
     vb = 8 if precision == 64 else 4
-    mat = (vb + 4) * nnz0 + (vb * D if q1_folded else (vb + 4) * nnz1)
+    cols = 4 * nnz0 if wide_entries is None else 2 * nnz0 + 2 * wide_entries
+    mat = vb * nnz0 + cols + (vb * D if q1_folded else (vb + 4) * nnz1)
     vec = 17 * vb * D + (16 * D if precision == 32 else 0)
     return (4 * mat + vec) / 4.0
+
+
+def wide_entries(info, p):
+    """Entries read with int32 columns when the stage kernel in use for precision slot p reads
+    the 16-bit columns (None: it reads int32 columns only): the long rows' entries and every
+    slot of the escaped rows."""
+    if not info.rk4_compact[p]:
+        return None
+    return info.tail_nnz + info.compact_escaped_rows * info.ell_width_q0
 
 
 def launches_per_call(n):
@@ -287,16 +298,19 @@ def main():
     ms_all, total_steps = R.reduce_timing(ms, args.steps * STEP_RK4, dist, "cuda")
     value = total_steps / (ms_all * 1e-3)
     avg_launch_ms = ms / (args.steps * STEP_RK4 * 4)
-    bytes_launch = stage_bytes(info.nnz_q0, info.nnz_q1, D, 64, bool(info.q1_folded))
+    info = G.gksl_get_info(ctx)   # with the stage kernel chosen at the first propagation
+    bytes_launch = stage_bytes(info.nnz_q0, info.nnz_q1, D, 64, bool(info.q1_folded), wide_entries(info, 0))
     hbm, peak_kind = peaks()
     achieved = bytes_launch / (avg_launch_ms * 1e-3) / 1e9
-    variant = G.gksl_get_info(ctx).rk4_variant[0]
-    kernel = KERNEL_OF_VARIANT.get(variant, "?").format(f="true" if info.q1_folded else "false")
+    variant = info.rk4_variant[0]
+    kernel = KERNEL_OF_VARIANT.get(variant, "?").format(f="true" if info.q1_folded else "false",
+                                                        c="true" if info.rk4_compact[0] else "false")
     traffic = None
     if os.path.exists(PROFILE_JSON):
         pj = json.load(open(PROFILE_JSON))
         if pj.get("src_hash") == src_hash():
-            traffic = pj.get("variants", {}).get(str(variant), {}).get("dram_bytes_per_launch")
+            key = f"{variant}{'c' if info.rk4_compact[0] else ''}"
+            traffic = pj.get("variants", {}).get(key, {}).get("dram_bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch,
                 "kernel": kernel + " (fused SpMV + RK4 stage update, FP64)"}
@@ -331,7 +345,8 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         ms32 = f0.elapsed_time(f1)
-        b32 = stage_bytes(info.nnz_q0, info.nnz_q1, D, 32, bool(info.q1_folded))
+        info = G.gksl_get_info(ctx)
+        b32 = stage_bytes(info.nnz_q0, info.nnz_q1, D, 32, bool(info.q1_folded), wide_entries(info, 1))
         extras["fp32_bulk"] = {"value": args.steps * STEP_RK4 / (ms32 * 1e-3), "unit": UNIT,
                                "achieved_gbs": b32 / (ms32 * 1e-3 / (args.steps * STEP_RK4 * 4)) / 1e9}
         # its error against the FP64 path after STEP_RK4 steps from rho0
@@ -350,8 +365,12 @@ def main():
         extras["steps_per_period_stable"] = spp
         tinfo = G.gksl_get_info(ctx)
         extras["stage_kernel_variant"] = {
-            p: {"chosen": tinfo.rk4_variant[i], "timed_us_per_step": [round(x, 2) for x in tinfo.rk4_variant_us[i]]}
+            p: {"chosen": tinfo.rk4_variant[i], "columns": 16 if tinfo.rk4_compact[i] else 32,
+                "timed_us_per_step": [round(x, 2) for x in tinfo.rk4_variant_us[i]],
+                "timed_us_per_step_16bit_columns": [round(x, 2) for x in tinfo.rk4_variant_us_c16[i]]}
             for i, p in enumerate(("fp64", "fp32"))}
+        extras["stage_columns_16bit"] = {"escaped_rows": tinfo.compact_escaped_rows, "long_rows": tinfo.long_rows,
+                                         "long_row_entries": tinfo.tail_nnz}
     G.gksl_destroy(ctx)
     if not args.no_extras and rank == 0:
         extras["matrix_free"] = matrix_free_extras(G, W, torch, stream, d, spp, args.steps)

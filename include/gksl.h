@@ -136,6 +136,15 @@ gksl_status gksl_structure_enumerate(int N, int which, long long capacity, int *
  * there and reads no Q1 column indices.  Both forms compute the same map; they differ by
  * rounding only. */
 #define GKSL_ASM_NO_FOLD 16u
+/* Build no 16-bit copy of the RK4 stage columns.  By default, when Q1 is folded, a copy holds
+ * each stored entry's column as a 16-bit offset from its row or from the row's S/J partner (the
+ * generator of the same pair (j, k) in the other half of the basis); rows with a column beyond
+ * +-16383 of both get threads of their own that read the 32-bit columns, and the long rows keep
+ * their warps.  The copy is dropped when more than one short row in eight would escape.  The
+ * first propagation times the stage kernels with either column width and keeps the fastest
+ * (gksl_info.rk4_compact); both compute the same map with the same arithmetic (bit-identical
+ * results). */
+#define GKSL_ASM_WIDE_COLUMNS 32u
 /* Matrix-free form: build no CSR matrix; keep H0 (+ E H1), H1, Gamma = 1/2 sum_p gamma_p L_p^+ L_p
  * and sqrt(gamma_p) L_p as complex diagonals (O(N) data) and let gksl_propagate apply Q(t) v + K on
  * the fly, as Tr(F_s L_t(rho)) with rho = 1/N + sum v F (Eq. 1, 6, 8), from tiles of rho rebuilt
@@ -281,6 +290,11 @@ typedef struct {
     int rk4_variant[2];           /* stage-kernel variant in use, [0]: FP64, [1]: FP32 (chosen by timing) */
     double rk4_variant_us[2][4];  /* timed cost per RK4 step of each variant, microseconds (0: not timed) */
     int q1_folded;                /* 1: Q1 folded into the propagation format (see GKSL_ASM_NO_FOLD) */
+    int compact_columns[2];       /* 1: 16-bit stage columns built (GKSL_ASM_WIDE_COLUMNS), [0]: FP64, [1]: FP32 */
+    long long compact_escaped_rows; /* short rows that read 32-bit columns in the 16-bit form */
+    long long tail_nnz;           /* stored entries of the long rows (read warp-per-row) */
+    int rk4_compact[2];           /* 1: the variant in use reads the 16-bit columns (chosen by timing with it) */
+    double rk4_variant_us_c16[2][4]; /* as rk4_variant_us, with 16-bit columns (0: not timed) */
 } gksl_info;
 
 gksl_status gksl_get_info(gksl_ctx *ctx, gksl_info *out);

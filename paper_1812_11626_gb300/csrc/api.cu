@@ -663,9 +663,17 @@ extern "C" gksl_status gksl_get_info(gksl_ctx *c, gksl_info *out) {
         out->assemble_seconds = c->assemble_seconds;
         out->max_abs_q0 = c->max_abs_q0;
         out->q1_folded = c->q1_folded ? 1 : 0;
+        out->compact_columns[0] = c->hyb0.ell_c16.p ? 1 : 0;
+        out->compact_columns[1] = c->hyb0f.ell_c16.p ? 1 : 0;
+        out->compact_escaped_rows = c->hyb0.ell_c16.p ? c->hyb0.n_esc : 0;
+        out->tail_nnz = c->hyb0.tail_nnz;
         for (int p = 0; p < 2; ++p) {
             out->rk4_variant[p] = c->rk4_var[p];
-            for (int v = 0; v < 4; ++v) out->rk4_variant_us[p][v] = c->rk4_var_us[p][v];
+            out->rk4_compact[p] = c->rk4_c16[p] && c->rk4_var[p] != 2 ? 1 : 0;
+            for (int v = 0; v < 4; ++v) {
+                out->rk4_variant_us[p][v] = c->rk4_var_us[p][v];
+                out->rk4_variant_us_c16[p][v] = c->rk4_var_us_c16[p][v];
+            }
         }
     });
 }

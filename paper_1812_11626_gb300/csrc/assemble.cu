@@ -590,6 +590,13 @@ void assemble(gksl_ctx *c, unsigned flags) {
     build_hyb_pair(q0e, c->Q1, D, c->hyb0, c->hyb1, fp32 ? &c->hyb0f : nullptr, fp32 ? &c->hyb1f : nullptr, s);
     c->q1_folded = !(flags & GKSL_ASM_NO_FOLD) &&
                    fold_q1(q0e, c->Q1, D, c->hyb0, fp32 ? &c->hyb0f : nullptr, c->q1v, c->q1vf, s);
+    // 16-bit relative columns for the folded stage stream (built from the final slot order)
+    c->hyb0.ell_c16.release();
+    c->hyb0f.ell_c16.release();
+    if (c->q1_folded && !(flags & GKSL_ASM_WIDE_COLUMNS)) {
+        build_c16(c->hyb0, c->P2, s);
+        if (fp32) build_c16(c->hyb0f, c->P2, s);
+    }
     c->has_adj = false;
     c->adj_n = 0;
     if (flags & GKSL_ASM_TRANSPOSE) {

@@ -283,11 +283,6 @@ __global__ void k_column(const double *__restrict__ V, long long rows, int B, in
     if (r < rows) out[r] = V[r * B + b];
 }
 
-__global__ void k_to_f32b(const double *__restrict__ v, float *__restrict__ o, long long n) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) o[i] = (float)v[i];
-}
-
 __global__ void k_set_base(long long *p, long long v) { *p = v; }
 
 struct Group {

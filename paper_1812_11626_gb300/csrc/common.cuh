@@ -115,11 +115,28 @@ struct Hyb {
     DBuf<int> tail_ptr;   // n_long + 1
     DBuf<int> tail_col;
     DBuf<VT> tail_val;
+    long long tail_nnz = 0;
+    // Compact copy of ell_col (empty when not built): slot entry e = (delta << 1) | s holds the
+    // column delta + (s ? partner(r) : r), partner(r) being the S/J partner of basis row r
+    // (r +- pairs for the S and J rows, r itself for the D rows), |delta| <= kC16Max.  Rows that
+    // do not fit (listed in c16_esc, read through ell_col by threads of their own) and long rows
+    // hold kC16Esc in slot 0.
+    DBuf<short> ell_c16;
+    long long c16_pairs = 0;   // N(N-1)/2
+    long long n_esc = 0;       // short rows read through ell_col
+    DBuf<int> c16_esc;
     size_t bytes() const {
         return ell_col.bytes() + ell_val.bytes() + long_rows.bytes() + tail_ptr.bytes() + tail_col.bytes() +
-               tail_val.bytes();
+               tail_val.bytes() + ell_c16.bytes() + c16_esc.bytes();
     }
 };
+
+constexpr int kC16Max = 16383;
+constexpr int kC16Esc = -32767;   // (-16384 << 1) | 1: a delta out of range, never a column
+
+__device__ __host__ inline long long c16_partner(long long r, long long pairs) {
+    return r < pairs ? r + pairs : (r < 2 * pairs ? r - pairs : r);
+}
 
 // Plain-pointer view of a Hyb matrix for kernels.
 template <typename VT>
@@ -131,11 +148,14 @@ struct HybView {
     const int *tail_ptr;
     const int *tail_col;
     const VT *tail_val;
+    const short *ell_c16;
+    long long c16_pairs;
 };
 
 template <typename VT>
 inline HybView<VT> view(const Hyb<VT> &h) {
-    return HybView<VT>{h.ell_col.p, h.ell_val.p, h.ld, h.width, h.tail_ptr.p, h.tail_col.p, h.tail_val.p};
+    return HybView<VT>{h.ell_col.p,  h.ell_val.p,  h.ld,        h.width,     h.tail_ptr.p,
+                       h.tail_col.p, h.tail_val.p, h.ell_c16.p, h.c16_pairs};
 }
 
 // Band data of the matrix-free form: the operators of L(rho) as complex diagonals, row-major
@@ -240,6 +260,8 @@ struct gksl_ctx {
     int rk4_var[2] = {0, 0};
     bool rk4_tuned[2] = {false, false};
     double rk4_var_us[2][4] = {};
+    bool rk4_c16[2] = {false, false};   // stage columns from Hyb::ell_c16 (chosen with the variant)
+    double rk4_var_us_c16[2][4] = {};
     // cached CUDA graphs for chunks of steps
     struct Graph {
         long long steps = 0;

@@ -114,6 +114,7 @@ void fill_one(const CsrR &a, double scale, long long rows, long long ld, int W, 
                                                       h.ell_col.p, h.ell_val.p);
     GK_LAUNCH_CHECK();
     h.n_long = nl;
+    h.tail_nnz = tnnz;
     h.tail_ptr.alloc((size_t)nl + 1);
     h.tail_col.alloc((size_t)(tnnz > 0 ? tnnz : 1));
     h.tail_val.alloc((size_t)(tnnz > 0 ? tnnz : 1));
@@ -235,7 +236,62 @@ __global__ void k_q1_fold(const int *__restrict__ q0_rowptr, const int *__restri
     q1v[r] = (VT)q1_val[q1_rowptr[r]];
 }
 
+// Compact columns of one row: each slot's column as a delta from the row (s = 0) or from its
+// S/J partner (s = 1), whichever fits in kC16Max; a long row or a row with a column that fits
+// neither way gets kC16Esc in slot 0, and the latter is flagged for the escape list.  Rows past
+// `rows` (padding up to ld) get zeros.
+__global__ void k_c16(const int *__restrict__ ell_col, long long ld, int W, long long rows, long long pairs,
+                      short *__restrict__ c16, long long *__restrict__ esc) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ld) return;
+    if (r >= rows) {
+        for (int j = 0; j < W; ++j) c16[(long long)j * ld + r] = 0;
+        return;
+    }
+    const long long pr = c16_partner(r, pairs);
+    bool ok = ell_col[r] >= 0;
+    for (int j = 0; j < W && ok; ++j) {
+        const long long p = (long long)j * ld + r;
+        const long long col = ell_col[p];
+        const long long d0 = col - r, d1 = col - pr;
+        if (d0 >= -kC16Max && d0 <= kC16Max) c16[p] = (short)(2 * d0);
+        else if (d1 >= -kC16Max && d1 <= kC16Max) c16[p] = (short)(2 * d1 + 1);
+        else ok = false;
+    }
+    if (!ok) c16[r] = (short)kC16Esc;
+    esc[r] = !ok && ell_col[r] >= 0;
+}
+
 }  // namespace
+
+template <typename VT>
+bool build_c16(Hyb<VT> &h, long long pairs, cudaStream_t s) {
+    h.ell_c16.release();
+    h.c16_esc.release();
+    h.c16_pairs = pairs;
+    h.n_esc = 0;
+    if (h.width < 1 || h.rows < 1) return false;
+    h.ell_c16.alloc((size_t)(h.ld * h.width));
+    DBuf<long long> flag((size_t)h.rows), pos((size_t)h.rows + 1);
+    k_c16<<<grid_for(h.ld, 256), 256, 0, s>>>(h.ell_col.p, h.ld, h.width, h.rows, pairs, h.ell_c16.p, flag.p);
+    GK_LAUNCH_CHECK();
+    const long long n = scan_ll(flag.p, pos.p, h.rows, true, true, s);
+    if (n * 8 > h.rows - h.n_long) {
+        h.ell_c16.release();
+        return false;
+    }
+    h.n_esc = n;
+    h.c16_esc.alloc((size_t)(n > 0 ? n : 1));
+    if (n > 0) {
+        k_long_list<<<grid_for(h.rows, 256), 256, 0, s>>>(flag.p, pos.p, h.rows, h.c16_esc.p);
+        GK_LAUNCH_CHECK();
+    }
+    GK_CUDA(cudaStreamSynchronize(s));
+    return true;
+}
+
+template bool build_c16<double>(Hyb<double> &, long long, cudaStream_t);
+template bool build_c16<float>(Hyb<float> &, long long, cudaStream_t);
 
 bool fold_q1(const CsrR &q0e, const CsrR &q1, long long rows, Hyb<double> &h0, Hyb<float> *h0f, DBuf<double> &q1v,
              DBuf<float> &q1vf, cudaStream_t s) {

@@ -70,6 +70,10 @@ void build_hyb_single(const CsrR &a, long long rows, Hyb<double> &h, Hyb<float> 
 // at most one Q1 entry and its column is among the row's entries; returns whether it did
 bool fold_q1(const CsrR &q0e, const CsrR &q1, long long rows, Hyb<double> &h0, Hyb<float> *h0f, DBuf<double> &q1v,
              DBuf<float> &q1vf, cudaStream_t s);
+// 16-bit relative copy of h's ELL columns (Hyb::ell_c16) for the S/J/D basis with `pairs` =
+// N(N-1)/2 pairs; kept when at most one short row in eight falls back to 32-bit columns
+template <typename VT>
+bool build_c16(Hyb<VT> &h, long long pairs, cudaStream_t s);
 // several matrices applied together (one long-row set; entries scaled by `scales`)
 void build_hyb_multi(const std::vector<const CsrR *> &ms, const std::vector<double> &scales, long long rows,
                      const std::vector<Hyb<double> *> &out, const std::vector<Hyb<float> *> &outf, cudaStream_t s);

@@ -43,24 +43,71 @@ __global__ void k_set_ll(long long *p, long long v) { *p = v; }
 template <typename VT>
 __device__ inline VT ldcs(const VT *p) { return __ldcs(p); }
 
-// sum over the ELL slots of row r (slot 0 already loaded as c0/a0)
-template <typename VT, typename AT, int W>
-__device__ inline AT ell_dot(const HybView<VT> &H, long long r, int c0, VT a0, const VT *__restrict__ y) {
+// column of a 16-bit ELL entry e of row r whose S/J partner is pr (Hyb::ell_c16)
+__device__ inline int c16_col(int e, int r, int pr) { return ((e & 1) ? pr : r) + (e >> 1); }
+
+// column of ELL slot position p of row r: from the 16-bit form (C) or the 32-bit one
+template <bool C, typename VT>
+__device__ inline int ell_c(const HybView<VT> &H, long long p, long long r, int pr) {
+    if constexpr (C) return c16_col(ldcs(H.ell_c16 + p), (int)r, pr);
+    else return ldcs(H.ell_col + p);
+}
+
+// all W columns of row r; c[0] = -1 for a row handled elsewhere (a long row, or with C a row
+// escaped from the 16-bit form)
+template <bool C, int W, typename VT>
+__device__ inline void ell_cols(const HybView<VT> &H, long long r, int (&c)[W]) {
+    if constexpr (C) {
+        const int e0 = ldcs(H.ell_c16 + r);
+        if (e0 == kC16Esc) {
+            c[0] = -1;
+            return;
+        }
+        const int pr = (int)c16_partner(r, H.c16_pairs);
+        c[0] = c16_col(e0, (int)r, pr);
+#pragma unroll
+        for (int j = 1; j < W; ++j) c[j] = ell_c<true>(H, (long long)j * H.ld + r, r, pr);
+    } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) c[j] = ldcs(H.ell_col + (long long)j * H.ld + r);
+    }
+}
+
+// sum over the ELL slots of row r (slot 0 already loaded as c0/a0; pr: r's S/J partner for C)
+template <typename VT, typename AT, int W, bool C>
+__device__ inline AT ell_dot(const HybView<VT> &H, long long r, int pr, int c0, VT a0, const VT *__restrict__ y) {
     AT s = (AT)a0 * (AT)__ldg(y + c0);
     if (W > 0) {
 #pragma unroll
         for (int j = 1; j < W; ++j) {
             long long p = (long long)j * H.ld + r;
-            s += (AT)ldcs(H.ell_val + p) * (AT)__ldg(y + ldcs(H.ell_col + p));
+            s += (AT)ldcs(H.ell_val + p) * (AT)__ldg(y + ell_c<C>(H, p, r, pr));
         }
     } else {
 #pragma unroll 4
         for (int j = 1; j < H.width; ++j) {
             long long p = (long long)j * H.ld + r;
-            s += (AT)ldcs(H.ell_val + p) * (AT)__ldg(y + ldcs(H.ell_col + p));
+            s += (AT)ldcs(H.ell_val + p) * (AT)__ldg(y + ell_c<C>(H, p, r, pr));
         }
     }
     return s;
+}
+
+// slot 0 of row r: its column (c0) and, for C, its S/J partner (pr); false for a row handled
+// elsewhere (a long row, or with C a row escaped from the 16-bit form)
+template <bool C, typename VT>
+__device__ inline bool ell_slot0(const HybView<VT> &H, long long r, int &c0, int &pr) {
+    pr = 0;
+    if constexpr (C) {
+        const int e0 = ldcs(H.ell_c16 + r);
+        if (e0 == kC16Esc) return false;
+        pr = (int)c16_partner(r, H.c16_pairs);
+        c0 = c16_col(e0, (int)r, pr);
+        return true;
+    } else {
+        c0 = ldcs(H.ell_col + r);
+        return c0 >= 0;
+    }
 }
 
 template <typename VT, typename AT>
@@ -95,6 +142,9 @@ struct StepArgs {
     HConst hc;
     const double *q1v;    // Q1 folded into slot 0 (M kernels): its value per row
     const float *q1vf;
+    const int *esc_rows;  // rows escaped from the 16-bit column form (C kernels), one thread each
+    long long n_esc;
+    int nb_esc;           // blocks of escaped rows, after the nb_long blocks of long rows
 };
 
 template <typename VT>
@@ -104,8 +154,35 @@ __device__ inline const double *q1_of<double>(const StepArgs &a) { return a.q1v;
 template <>
 __device__ inline const float *q1_of<float>(const StepArgs &a) { return a.q1vf; }
 
+// One ELL row of the stage: k_r from slot 0 (plus the folded Q1 value for M) and the other
+// slots, then the stage update; nothing for a row handled elsewhere.
+template <int STAGE, int W, typename VT, bool M, bool C>
+__device__ inline void ell_row(const HybView<VT> &A0, const HybView<VT> &A1, const StepArgs &a, VT eps, long long r,
+                               const VT *__restrict__ y, VT *v, double *v64, VT *__restrict__ yn,
+                               VT *__restrict__ acc) {
+    int c0, pr;
+    if (!ell_slot0<C>(A0, r, c0, pr)) return;
+    VT a0 = ldcs(A0.ell_val + r);
+    if (M) a0 = fma(eps, ldcs(q1_of<VT>(a) + r), a0);
+    VT s0 = ell_dot<VT, VT, W, C>(A0, r, pr, c0, a0, y);
+    if (!M) s0 = s0 + eps * ell_dot_full<VT, VT>(A1, r, y);
+    epi<STAGE, VT>(r, s0, v, v64, yn, acc, a.hc);
+}
+
+// Blocks [nb_long, nb_long + nb_esc) of a C launch: the rows escaped from the 16-bit column form,
+// one thread each, through the 32-bit columns.  Returns whether this block is one of them.
+template <int STAGE, int W, typename VT, bool M, bool C>
+__device__ inline bool esc_rows_part(const HybView<VT> &A0, const HybView<VT> &A1, const StepArgs &a, VT eps,
+                                     const VT *__restrict__ y, VT *v, double *v64, VT *yn, VT *acc) {
+    if (!C || (int)blockIdx.x >= a.nb_long + a.nb_esc) return false;
+    const long long i = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
+    if (i < a.n_esc) ell_row<STAGE, W, VT, M, false>(A0, A1, a, eps, a.esc_rows[i], y, v, v64, yn, acc);
+    return true;
+}
+
 // M: Q1 folded into slot 0 (slot 0 holds q0 + (eps - E) q1, no Q1 ELL is read)
-template <int STAGE, int W, bool M>
+// C: columns from the 16-bit form (Hyb::ell_c16), with M only
+template <int STAGE, int W, bool M, bool C>
 __global__ void __launch_bounds__(kThreads) k_stage64(HybView<double> A0, HybView<double> A1, StepArgs a,
                                                       const double *__restrict__ y, double *v, double *__restrict__ yn,
                                                       double *__restrict__ acc) {
@@ -122,18 +199,12 @@ __global__ void __launch_bounds__(kThreads) k_stage64(HybView<double> A0, HybVie
         if (lane == 0) epi64<STAGE>(a.long_rows[i], s0 + eps * s1, v, yn, acc, a.hc);
         return;
     }
-    long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
-    if (r >= a.D) return;
-    int c0 = ldcs(A0.ell_col + r);
-    if (c0 < 0) return;   // long row, handled by a warp above
-    double a0 = ldcs(A0.ell_val + r);
-    if (M) a0 = fma(eps, ldcs(a.q1v + r), a0);
-    double s0 = ell_dot<double, double, W>(A0, r, c0, a0, y);
-    if (!M) s0 = s0 + eps * ell_dot_full<double, double>(A1, r, y);
-    epi64<STAGE>(r, s0, v, yn, acc, a.hc);
+    if (esc_rows_part<STAGE, W, double, M, C>(A0, A1, a, eps, y, v, nullptr, yn, acc)) return;
+    long long r = (long long)(blockIdx.x - a.nb_long - a.nb_esc) * kThreads + threadIdx.x;
+    if (r < a.D) ell_row<STAGE, W, double, M, C>(A0, A1, a, eps, r, y, v, nullptr, yn, acc);
 }
 
-template <int STAGE, int W, bool M>
+template <int STAGE, int W, bool M, bool C>
 __global__ void __launch_bounds__(kThreads) k_stage32(HybView<float> A0, HybView<float> A1, StepArgs a,
                                                       const float *__restrict__ y, float *v32, double *v64,
                                                       float *__restrict__ yn, float *__restrict__ acc) {
@@ -150,15 +221,9 @@ __global__ void __launch_bounds__(kThreads) k_stage32(HybView<float> A0, HybView
         if (lane == 0) epi32<STAGE>(a.long_rows[i], s0 + eps * s1, v32, v64, yn, acc, a.hc);
         return;
     }
-    long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
-    if (r >= a.D) return;
-    int c0 = ldcs(A0.ell_col + r);
-    if (c0 < 0) return;
-    float a0 = ldcs(A0.ell_val + r);
-    if (M) a0 = fmaf(eps, ldcs(a.q1vf + r), a0);
-    float s0 = ell_dot<float, float, W>(A0, r, c0, a0, y);
-    if (!M) s0 = s0 + eps * ell_dot_full<float, float>(A1, r, y);
-    epi32<STAGE>(r, s0, v32, v64, yn, acc, a.hc);
+    if (esc_rows_part<STAGE, W, float, M, C>(A0, A1, a, eps, y, v32, v64, yn, acc)) return;
+    long long r = (long long)(blockIdx.x - a.nb_long - a.nb_esc) * kThreads + threadIdx.x;
+    if (r < a.D) ell_row<STAGE, W, float, M, C>(A0, A1, a, eps, r, y, v32, v64, yn, acc);
 }
 
 // ---- variants of the ELL part (same arithmetic, same summation order per row)
@@ -179,7 +244,7 @@ __device__ inline bool long_rows_part(const HybView<VT> &A0, const HybView<VT> &
 
 // Variant 1: the whole ELL row is loaded into registers (all columns, then all values, then
 // all gathers) before the products, with a larger register budget for the loads in flight.
-template <int STAGE, int W, typename VT, bool M>
+template <int STAGE, int W, typename VT, bool M, bool C>
 __global__ void __launch_bounds__(kThreads, 3) k_stage_pf(HybView<VT> A0, HybView<VT> A1, StepArgs a,
                                                           const VT *__restrict__ y, VT *v, double *v64,
                                                           VT *__restrict__ yn, VT *__restrict__ acc) {
@@ -188,12 +253,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_stage_pf(HybView<VT> A0, HybVie
     __syncthreads();
     const VT eps = s_eps;
     if (long_rows_part<STAGE, VT>(A0, A1, a, eps, y, v, v64, yn, acc)) return;
-    long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
+    if (esc_rows_part<STAGE, W, VT, M, C>(A0, A1, a, eps, y, v, v64, yn, acc)) return;
+    long long r = (long long)(blockIdx.x - a.nb_long - a.nb_esc) * kThreads + threadIdx.x;
     if (r >= a.D) return;
     int c[W];
     VT x[W], m[W];
-#pragma unroll
-    for (int j = 0; j < W; ++j) c[j] = ldcs(A0.ell_col + (long long)j * A0.ld + r);
+    ell_cols<C, W>(A0, r, c);
     if (c[0] < 0) return;
 #pragma unroll
     for (int j = 0; j < W; ++j) m[j] = ldcs(A0.ell_val + (long long)j * A0.ld + r);
@@ -213,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_stage_pf(HybView<VT> A0, HybVie
 // reads the drive table, the step base or a state vector, or writes anything.  The next stage's
 // blocks thus take the SMs the previous stage frees in its last wave and stream their matrix
 // slots meanwhile.
-template <int STAGE, int W, typename VT, bool M>
+template <int STAGE, int W, typename VT, bool M, bool C>
 __global__ void __launch_bounds__(kThreads, 3) k_stage_pdl(HybView<VT> A0, HybView<VT> A1, StepArgs a,
                                                            const VT *__restrict__ y, VT *v, double *v64,
                                                            VT *__restrict__ yn, VT *__restrict__ acc) {
@@ -230,20 +295,25 @@ __global__ void __launch_bounds__(kThreads, 3) k_stage_pdl(HybView<VT> A0, HybVi
         }
         return;
     }
-    const long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x;
+    if (C && (int)blockIdx.x < a.nb_long + a.nb_esc) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        const VT eps = (VT)a.eps_tab[3 * (*a.base + a.local) + eps_slot<STAGE>()];
+        esc_rows_part<STAGE, W, VT, M, C>(A0, A1, a, eps, y, v, v64, yn, acc);
+        return;
+    }
+    const long long r = (long long)(blockIdx.x - a.nb_long - a.nb_esc) * kThreads + threadIdx.x;
     const bool in = r < a.D;
     int c[W];
     VT m[W];
     VT q = VT(0);
     if (in) {
-#pragma unroll
-        for (int j = 0; j < W; ++j) c[j] = ldcs(A0.ell_col + (long long)j * A0.ld + r);
+        ell_cols<C, W>(A0, r, c);
 #pragma unroll
         for (int j = 0; j < W; ++j) m[j] = ldcs(A0.ell_val + (long long)j * A0.ld + r);
         if (M) q = ldcs(q1_of<VT>(a) + r);
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (!in || c[0] < 0) return;   // past the end, or a long row (handled by a warp above)
+    if (!in || c[0] < 0) return;   // past the end, or a row handled above (long or escaped)
     const VT eps = (VT)a.eps_tab[3 * (*a.base + a.local) + eps_slot<STAGE>()];
     if (M) m[0] = eps * q + m[0];
     VT x[W];
@@ -348,6 +418,9 @@ Launch make_launch(gksl_ctx *c, const Hyb<double> &h0, double h, const double *t
     L.a.hc.h6f = (float)(h / 6.0);
     L.a.q1v = c->q1_folded ? c->q1v.p : nullptr;
     L.a.q1vf = c->q1_folded ? c->q1vf.p : nullptr;
+    L.a.esc_rows = nullptr;
+    L.a.n_esc = 0;
+    L.a.nb_esc = 0;
     L.grid = (unsigned)(L.a.nb_long + (c->D + kThreads - 1) / kThreads);
     return L;
 }
@@ -370,28 +443,28 @@ void launch_pdl(void (*kernel)(P...), unsigned grid, cudaStream_t s, A... args) 
     GK_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
 }
 
-template <int W, bool M>
+template <int W, bool M, bool C>
 void step64_w(gksl_ctx *c, const Launch &L, double *y2, double *y3, double *y4) {
     auto A0 = view(c->hyb0), A1 = view(c->hyb1);
     cudaStream_t s = c->stream;
-    k_stage64<1, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v.p, c->v.p, y2, c->acc.p);
-    k_stage64<2, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v.p, y3, c->acc.p);
-    k_stage64<3, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v.p, y4, c->acc.p);
-    k_stage64<4, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v.p, nullptr, c->acc.p);
+    k_stage64<1, W, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v.p, c->v.p, y2, c->acc.p);
+    k_stage64<2, W, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v.p, y3, c->acc.p);
+    k_stage64<3, W, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v.p, y4, c->acc.p);
+    k_stage64<4, W, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v.p, nullptr, c->acc.p);
 }
 
-template <int W, bool M>
+template <int W, bool M, bool C>
 void step32_w(gksl_ctx *c, const Launch &L, float *y2, float *y3, float *y4) {
     auto A0 = view(c->hyb0f), A1 = view(c->hyb1f);
     cudaStream_t s = c->stream;
-    k_stage32<1, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v32.p, c->v32.p, c->v.p, y2, c->acc32.p);
-    k_stage32<2, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v32.p, c->v.p, y3, c->acc32.p);
-    k_stage32<3, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v32.p, c->v.p, y4, c->acc32.p);
-    k_stage32<4, W, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v32.p, c->v.p, nullptr, c->acc32.p);
+    k_stage32<1, W, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, c->v32.p, c->v32.p, c->v.p, y2, c->acc32.p);
+    k_stage32<2, W, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, c->v32.p, c->v.p, y3, c->acc32.p);
+    k_stage32<3, W, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, c->v32.p, c->v.p, y4, c->acc32.p);
+    k_stage32<4, W, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, c->v32.p, c->v.p, nullptr, c->acc32.p);
 }
 
-// variants 1, 2 and 3 on either precision
-template <int VAR, int W, typename VT, bool M>
+// variants 1, 2 and 3 on either precision (variant 2 reads 32-bit columns only)
+template <int VAR, int W, typename VT, bool M, bool C>
 void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h1, VT *v, double *v64, VT *y2, VT *y3,
               VT *y4, VT *acc) {
     auto A0 = view(h0), A1 = view(h1);
@@ -399,15 +472,16 @@ void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h
     Launch L = L0;
     if (VAR == 2) L.grid = (unsigned)(L.a.nb_long + (c->D + 2 * kThreads - 1) / (2 * kThreads));
     if constexpr (VAR == 3) {
-        launch_pdl(k_stage_pdl<1, W, VT, M>, L.grid, s, A0, A1, L.a, (const VT *)v, v, v64, y2, acc);
-        launch_pdl(k_stage_pdl<2, W, VT, M>, L.grid, s, A0, A1, L.a, (const VT *)y2, v, v64, y3, acc);
-        launch_pdl(k_stage_pdl<3, W, VT, M>, L.grid, s, A0, A1, L.a, (const VT *)y3, v, v64, y4, acc);
-        launch_pdl(k_stage_pdl<4, W, VT, M>, L.grid, s, A0, A1, L.a, (const VT *)y4, v, v64, (VT *)nullptr, acc);
+        launch_pdl(k_stage_pdl<1, W, VT, M, C>, L.grid, s, A0, A1, L.a, (const VT *)v, v, v64, y2, acc);
+        launch_pdl(k_stage_pdl<2, W, VT, M, C>, L.grid, s, A0, A1, L.a, (const VT *)y2, v, v64, y3, acc);
+        launch_pdl(k_stage_pdl<3, W, VT, M, C>, L.grid, s, A0, A1, L.a, (const VT *)y3, v, v64, y4, acc);
+        launch_pdl(k_stage_pdl<4, W, VT, M, C>, L.grid, s, A0, A1, L.a, (const VT *)y4, v, v64, (VT *)nullptr,
+                   acc);
     } else if constexpr (VAR == 1) {
-        k_stage_pf<1, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
-        k_stage_pf<2, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
-        k_stage_pf<3, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, v, v64, y4, acc);
-        k_stage_pf<4, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, v, v64, nullptr, acc);
+        k_stage_pf<1, W, VT, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
+        k_stage_pf<2, W, VT, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
+        k_stage_pf<3, W, VT, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y3, v, v64, y4, acc);
+        k_stage_pf<4, W, VT, M, C><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y4, v, v64, nullptr, acc);
     } else {
         k_stage_r2<1, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, v, v, v64, y2, acc);
         k_stage_r2<2, W, VT, M><<<L.grid, kThreads, 0, s>>>(A0, A1, L.a, y2, v, v64, y3, acc);
@@ -417,40 +491,52 @@ void step_var(gksl_ctx *c, const Launch &L0, const Hyb<VT> &h0, const Hyb<VT> &h
 }
 
 // CSR-form step with explicit stage-input buffers (null: the context's yA, yB, yA)
-template <bool M>
+template <bool M, bool C>
 void launch_step_csr_t(gksl_ctx *c, int precision, double h, const double *tab, long long local, void *Y2, void *Y3,
                        void *Y4) {
     Launch L = make_launch(c, c->hyb0, h, tab, local);
     int W = c->hyb0.width;
     int var = c->rk4_var[precision == 64 ? 0 : 1];
     if ((var == 1 || var == 3) && W != 18) var = 0;   // the register-prefetch variants exist for 18 slots only
+    if (C && var != 2) {   // blocks for the rows escaped from the 16-bit columns
+        const long long n_esc = precision == 64 ? c->hyb0.n_esc : c->hyb0f.n_esc;
+        L.a.esc_rows = precision == 64 ? c->hyb0.c16_esc.p : c->hyb0f.c16_esc.p;
+        L.a.n_esc = n_esc;
+        L.a.nb_esc = (int)((n_esc + kThreads - 1) / kThreads);
+        L.grid += (unsigned)L.a.nb_esc;
+    }
     if (precision == 64) {
         double *y2 = Y2 ? (double *)Y2 : c->yA.p, *y3 = Y3 ? (double *)Y3 : c->yB.p, *y4 = Y4 ? (double *)Y4 : c->yA.p;
-        if (var == 3) step_var<3, 18, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
-        else if (var == 1) step_var<1, 18, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
-        else if (var == 2 && W == 18)
-            step_var<2, 18, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
-        else if (var == 2) step_var<2, 0, double, M>(c, L, c->hyb0, c->hyb1, c->v.p, nullptr, y2, y3, y4, c->acc.p);
-        else if (W == 18) step64_w<18, M>(c, L, y2, y3, y4);
-        else step64_w<0, M>(c, L, y2, y3, y4);
+        const Hyb<double> &h0 = c->hyb0, &h1 = c->hyb1;
+        double *v = c->v.p, *acc = c->acc.p;
+        if (var == 3) step_var<3, 18, double, M, C>(c, L, h0, h1, v, nullptr, y2, y3, y4, acc);
+        else if (var == 1) step_var<1, 18, double, M, C>(c, L, h0, h1, v, nullptr, y2, y3, y4, acc);
+        else if (var == 2 && W == 18) step_var<2, 18, double, M, false>(c, L, h0, h1, v, nullptr, y2, y3, y4, acc);
+        else if (var == 2) step_var<2, 0, double, M, false>(c, L, h0, h1, v, nullptr, y2, y3, y4, acc);
+        else if (W == 18) step64_w<18, M, C>(c, L, y2, y3, y4);
+        else step64_w<0, M, C>(c, L, y2, y3, y4);
     } else {
         float *y2 = Y2 ? (float *)Y2 : c->yA32.p, *y3 = Y3 ? (float *)Y3 : c->yB32.p, *y4 = Y4 ? (float *)Y4 : c->yA32.p;
-        if (var == 3) step_var<3, 18, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
-        else if (var == 1) step_var<1, 18, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
-        else if (var == 2 && W == 18)
-            step_var<2, 18, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
-        else if (var == 2)
-            step_var<2, 0, float, M>(c, L, c->hyb0f, c->hyb1f, c->v32.p, c->v.p, y2, y3, y4, c->acc32.p);
-        else if (W == 18) step32_w<18, M>(c, L, y2, y3, y4);
-        else step32_w<0, M>(c, L, y2, y3, y4);
+        const Hyb<float> &h0 = c->hyb0f, &h1 = c->hyb1f;
+        float *v = c->v32.p, *acc = c->acc32.p;
+        double *v64 = c->v.p;
+        if (var == 3) step_var<3, 18, float, M, C>(c, L, h0, h1, v, v64, y2, y3, y4, acc);
+        else if (var == 1) step_var<1, 18, float, M, C>(c, L, h0, h1, v, v64, y2, y3, y4, acc);
+        else if (var == 2 && W == 18) step_var<2, 18, float, M, false>(c, L, h0, h1, v, v64, y2, y3, y4, acc);
+        else if (var == 2) step_var<2, 0, float, M, false>(c, L, h0, h1, v, v64, y2, y3, y4, acc);
+        else if (W == 18) step32_w<18, M, C>(c, L, y2, y3, y4);
+        else step32_w<0, M, C>(c, L, y2, y3, y4);
     }
     GK_LAUNCH_CHECK();
 }
 
 void launch_step_csr(gksl_ctx *c, int precision, double h, const double *tab, long long local, void *Y2, void *Y3,
                      void *Y4) {
-    if (c->q1_folded) launch_step_csr_t<true>(c, precision, h, tab, local, Y2, Y3, Y4);
-    else launch_step_csr_t<false>(c, precision, h, tab, local, Y2, Y3, Y4);
+    const int pi = precision == 64 ? 0 : 1;
+    const bool cmp = (pi == 0 ? c->hyb0.ell_c16.p : c->hyb0f.ell_c16.p) != nullptr && c->rk4_c16[pi];
+    if (c->q1_folded && cmp) launch_step_csr_t<true, true>(c, precision, h, tab, local, Y2, Y3, Y4);
+    else if (c->q1_folded) launch_step_csr_t<true, false>(c, precision, h, tab, local, Y2, Y3, Y4);
+    else launch_step_csr_t<false, false>(c, precision, h, tab, local, Y2, Y3, Y4);
 }
 
 void launch_step(gksl_ctx *c, int precision, double h, const double *tab, long long local) {
@@ -463,16 +549,24 @@ void launch_step(gksl_ctx *c, int precision, double h, const double *tab, long l
 
 cudaGraphExec_t graph_for(gksl_ctx *c, long long steps, int precision, double h, const double *tab);
 
-// Time the stage-kernel variants on this context's matrix, each as a CUDA graph of 8 steps as
-// propagation replays them (from a saved copy of the state, which is restored afterwards), and
-// keep the fastest (best of two timed replays).  Systems below D = 1024 keep variant 0.
-// GKSL_RK4_VARIANT=0..3 forces a variant.
+// Time the stage-kernel variants on this context's matrix, each with 32-bit and (where built)
+// 16-bit columns, as a CUDA graph of 8 steps as propagation replays them (from a saved copy of
+// the state, which is restored afterwards; best of two timed replays), and keep the fastest; the
+// 16-bit columns only when they beat the best 32-bit variant by 2 % (where the FP64 pipe, not
+// the matrix stream, bounds the stage the two tie, and the 32-bit form has no escaped rows).
+// Systems below D = 1024 keep variant 0 (16-bit columns where built).  GKSL_RK4_VARIANT=0..3
+// forces a variant, GKSL_RK4_COLUMNS=32 the 32-bit columns.
 void tune_variant(gksl_ctx *c, int precision, double h, const double *tab) {
     constexpr int kSteps = 8;
     int pi = precision == 64 ? 0 : 1;
     if (c->rk4_tuned[pi]) return;
     c->rk4_tuned[pi] = true;
     if (c->asm_flags & GKSL_ASM_MATRIX_FREE) return;   // one matrix-free kernel per stage
+    const char *envc = getenv("GKSL_RK4_COLUMNS");
+    const bool have16 = (pi == 0 ? c->hyb0.ell_c16.p : c->hyb0f.ell_c16.p) != nullptr &&
+                        !(envc && envc[0] == '3' && envc[1] == '2');
+    c->rk4_c16[pi] = have16;
+    for (int var = 0; var < 4; ++var) c->rk4_var_us[pi][var] = c->rk4_var_us_c16[pi][var] = 0.0;
     const char *env = getenv("GKSL_RK4_VARIANT");
     if (env && env[0] >= '0' && env[0] <= '3') {
         c->rk4_var[pi] = env[0] - '0';
@@ -486,12 +580,15 @@ void tune_variant(gksl_ctx *c, int precision, double h, const double *tab) {
     cudaEvent_t e0, e1;
     GK_CUDA(cudaEventCreate(&e0));
     GK_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_v = 0;
-    for (int var = 0; var < 4; ++var) {
-        c->rk4_var_us[pi][var] = 0.0;
+    float best[2] = {1e30f, 1e30f};   // [column form]: 32-bit, 16-bit
+    int best_v[2] = {0, 0};
+    for (int k = 0; k < 8; ++k) {
+        const int var = k >> 1;
+        const bool c16 = k & 1;
         if ((var == 1 || var == 3) && c->hyb0.width != 18) continue;   // 18-slot layouts only
+        if (c16 && (!have16 || var == 2)) continue;                     // variant 2 reads 32-bit columns
         c->rk4_var[pi] = var;
+        c->rk4_c16[pi] = c16;
         cudaGraphExec_t g = graph_for(c, kSteps, precision, h, tab);
         k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, 0);
         GK_LAUNCH_CHECK();
@@ -508,12 +605,17 @@ void tune_variant(gksl_ctx *c, int precision, double h, const double *tab) {
             GK_CUDA(cudaEventElapsedTime(&t, e0, e1));
             ms = std::min(ms, t);
         }
-        c->rk4_var_us[pi][var] = 1000.0 * ms / kSteps;
-        if (ms < best) { best = ms; best_v = var; }
+        (c16 ? c->rk4_var_us_c16 : c->rk4_var_us)[pi][var] = 1000.0 * ms / kSteps;
+        if (ms < best[c16]) {
+            best[c16] = ms;
+            best_v[c16] = var;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->rk4_var[pi] = best_v;
+    const bool use16 = best[1] < 0.98f * best[0];
+    c->rk4_var[pi] = best_v[use16];
+    c->rk4_c16[pi] = use16;
     GK_CUDA(cudaMemcpyAsync(c->v.p, save.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, c->stream));
     if (precision == 32) {
         k_to_f32<<<grid_for(D1, 256), 256, 0, c->stream>>>(c->v.p, c->v32.p, D1);
@@ -524,7 +626,8 @@ void tune_variant(gksl_ctx *c, int precision, double h, const double *tab) {
 
 // one CUDA graph per (chunk length, precision, h); replayed with the step base set before
 cudaGraphExec_t graph_for(gksl_ctx *c, long long steps, int precision, double h, const double *tab) {
-    const int var = c->rk4_var[precision == 64 ? 0 : 1];
+    const int pi = precision == 64 ? 0 : 1;
+    const int var = c->rk4_var[pi] + (c->rk4_c16[pi] ? 4 : 0);
     for (auto &g : c->graphs)
         if (g.steps == steps && g.precision == precision && g.h == h && g.variant == var) return g.exec;
     cudaGraph_t graph;

@@ -21,6 +21,7 @@ GKSL_MAX_H0 = 8
 GKSL_MAX_P = 8
 GKSL_STRUCT_F, GKSL_STRUCT_D = 0, 1
 GKSL_ASM_FP32, GKSL_ASM_TRANSPOSE, GKSL_ASM_NO_DROP, GKSL_ASM_MATRIX_FREE, GKSL_ASM_NO_FOLD = 1, 2, 4, 8, 16
+GKSL_ASM_WIDE_COLUMNS = 32
 GKSL_MAT_Q0, GKSL_MAT_Q1, GKSL_MAT_H0, GKSL_MAT_R = 0, 1, 16, 32
 
 if not os.path.exists(LIB_PATH):
@@ -41,7 +42,10 @@ class gksl_info(ctypes.Structure):
                 ("ell_width_q0", ctypes.c_int), ("ell_width_q1", ctypes.c_int), ("long_rows", ctypes.c_longlong),
                 ("device_bytes", ctypes.c_longlong), ("assemble_seconds", ctypes.c_double),
                 ("max_abs_q0", ctypes.c_double), ("rk4_variant", ctypes.c_int * 2),
-                ("rk4_variant_us", (ctypes.c_double * 4) * 2), ("q1_folded", ctypes.c_int)]
+                ("rk4_variant_us", (ctypes.c_double * 4) * 2), ("q1_folded", ctypes.c_int),
+                ("compact_columns", ctypes.c_int * 2), ("compact_escaped_rows", ctypes.c_longlong),
+                ("tail_nnz", ctypes.c_longlong), ("rk4_compact", ctypes.c_int * 2),
+                ("rk4_variant_us_c16", (ctypes.c_double * 4) * 2)]
 
 
 _P = ctypes.c_void_p

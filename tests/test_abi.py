@@ -54,3 +54,34 @@ def test_create_without_device_fails_cleanly(G):
     with pytest.raises(G.GkslError) as e:
         G.gksl_create(4, 0)
     assert e.value.status == G.GKSL_ERR_CUDA
+
+
+def test_flag_constants_match_header(G):
+    """Every GKSL_* constant that both the header and the binding define has the same value."""
+    hdr = open(os.path.join(ROOT, "include", "gksl.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(GKSL_[A-Z0-9_]+)\s+(\d+)u?\b", hdr)}
+    assert "GKSL_ASM_WIDE_COLUMNS" in defs
+    shared = [k for k in defs if hasattr(G, k)]
+    assert len(shared) >= 6
+    for k in shared:
+        assert getattr(G, k) == defs[k], k
+
+
+def test_info_struct_layout_matches_header(G, tmp_path):
+    """The binding's gksl_info has the size and field offsets that a C compiler gives the
+    header's struct (compiled here with gcc)."""
+    import ctypes
+    fields = [f for f, _ in G.gksl_info._fields_]
+    src = tmp_path / "info.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gksl.h"', "int main(void) {",
+             '  printf("size %zu\\n", sizeof(gksl_info));']
+    lines += [f'  printf("{f} %zu\\n", offsetof(gksl_info, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "info"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(G.gksl_info)
+    for f in fields:
+        assert int(out[f]) == getattr(G.gksl_info, f).offset, f

@@ -324,6 +324,62 @@ def test_smallest_and_degenerate_systems(G):
         G.gksl_destroy(ctx)
 
 
+def test_compact_columns_match_wide(G):
+    """16-bit stage columns (the default once Q1 is folded) against 32-bit columns
+    (GKSL_ASM_WIDE_COLUMNS): the same stored entries in the same slot order and the same
+    arithmetic, so every stage-kernel variant gives bit-identical states in both precisions.  At
+    N = 200 some short rows reach a column farther than 16383 from both the row and its S/J
+    partner and take the 32-bit path inside the 16-bit form."""
+    import os
+    d = W.dimer(200)
+    D = d.N * d.N - 1
+    spp, n = 20000, 120
+    outs = {}
+    for wide in (False, True):
+        flags = G.GKSL_ASM_FP32 | (G.GKSL_ASM_WIDE_COLUMNS if wide else 0)
+        ctx = G.dimer_context(d, flags=flags)
+        try:
+            info = G.gksl_get_info(ctx)
+            assert info.q1_folded == 1
+            assert list(info.compact_columns) == ([0, 0] if wide else [1, 1])
+            assert wide or 0 < info.compact_escaped_rows < D // 8
+            for var in ("0", "1", "2", "3"):
+                os.environ["GKSL_RK4_VARIANT"] = var
+                try:
+                    for prec in (64, 32):
+                        G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+                        outs[(wide, var, prec)] = run_gpu(G, ctx, spp, n, n, precision=prec, D=D)[0]
+                        used = G.gksl_get_info(ctx).rk4_compact[0 if prec == 64 else 1]
+                        assert used == (0 if wide or var == "2" else 1)
+                finally:
+                    del os.environ["GKSL_RK4_VARIANT"]
+                G.gksl_assemble(ctx, flags)
+            if not wide:
+                # the 32-bit columns forced on a context that has the 16-bit ones
+                os.environ["GKSL_RK4_VARIANT"], os.environ["GKSL_RK4_COLUMNS"] = "0", "32"
+                try:
+                    G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+                    outs[(True, "0f", 64)] = run_gpu(G, ctx, spp, n, n, precision=64, D=D)[0]
+                    assert G.gksl_get_info(ctx).rk4_compact[0] == 0
+                finally:
+                    del os.environ["GKSL_RK4_VARIANT"], os.environ["GKSL_RK4_COLUMNS"]
+                # no override: the first propagation times every variant with both column widths
+                G.gksl_assemble(ctx, flags)
+                G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+                run_gpu(G, ctx, spp, 8, 8, precision=64, D=D)
+                info = G.gksl_get_info(ctx)
+                assert all(info.rk4_variant_us[0][v] > 0 for v in range(4))
+                assert [info.rk4_variant_us_c16[0][v] > 0 for v in range(4)] == [True, True, False, True]
+        finally:
+            G.gksl_destroy(ctx)
+    assert np.array_equal(outs[(True, "0f", 64)], outs[(True, "0", 64)])
+    for var in ("0", "1", "2", "3"):
+        for prec in (64, 32):
+            a, b = outs[(False, var, prec)], outs[(True, var, prec)]
+            assert np.isfinite(a).all() and np.abs(a).max() > 0
+            assert np.array_equal(a, b), (var, prec, np.abs(a - b).max())
+
+
 def test_folded_q1_matches_separate_stream(G):
     """Q1 folded into the propagation format (the default for the dimer, whose H1 is diagonal)
     against Q1 as a separate stream (GKSL_ASM_NO_FOLD): the same RK4 map up to rounding, in
