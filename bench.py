@@ -31,8 +31,16 @@ UNIT = "RK4 steps/s"
 PROFILE_JSON = os.path.join(ROOT, "profiles", "rk4_stage_fp64_n1000.json")
 # stage kernel of each variant of the library (chosen per context by timing; {f}: Q1 folded into
 # slot 0, {c}: 16-bit columns); variant 3 is launched with programmatic dependent launch
-KERNEL_OF_VARIANT = {0: "k_stage64<S,18,{f},{c}>", 1: "k_stage_pf<S,18,double,{f},{c}>",
-                     2: "k_stage_r2<S,18,double,{f}>", 3: "k_stage_pdl<S,18,double,{f},{c}>"}
+KERNEL_OF_VARIANT = {0: "k_stage{b}<S,18,{f},{c}>", 1: "k_stage_pf<S,18,{t},{f},{c}>",
+                     2: "k_stage_r2<S,18,{t},{f}>", 3: "k_stage_pdl<S,18,{t},{f},{c}>"}
+
+
+def kernel_name(info, p):
+    """Stage kernel in use for precision slot p (0: FP64, 1: FP32) after the variant timer ran."""
+    v = info.rk4_variant[p]
+    return KERNEL_OF_VARIANT.get(v, "?").format(b="64" if p == 0 else "32", t="double" if p == 0 else "float",
+                                                f="true" if info.q1_folded else "false",
+                                                c="true" if info.rk4_compact[p] else "false")
 
 
 def dist_env():
@@ -303,8 +311,7 @@ def main():
     hbm, peak_kind = peaks()
     achieved = bytes_launch / (avg_launch_ms * 1e-3) / 1e9
     variant = info.rk4_variant[0]
-    kernel = KERNEL_OF_VARIANT.get(variant, "?").format(f="true" if info.q1_folded else "false",
-                                                        c="true" if info.rk4_compact[0] else "false")
+    kernel = kernel_name(info, 0)
     traffic = None
     if os.path.exists(PROFILE_JSON):
         pj = json.load(open(PROFILE_JSON))
@@ -348,6 +355,7 @@ def main():
         info = G.gksl_get_info(ctx)
         b32 = stage_bytes(info.nnz_q0, info.nnz_q1, D, 32, bool(info.q1_folded), wide_entries(info, 1))
         extras["fp32_bulk"] = {"value": args.steps * STEP_RK4 / (ms32 * 1e-3), "unit": UNIT,
+                               "kernel": kernel_name(info, 1), "algorithmic_bytes_per_launch": b32,
                                "achieved_gbs": b32 / (ms32 * 1e-3 / (args.steps * STEP_RK4 * 4)) / 1e9}
         # its error against the FP64 path after STEP_RK4 steps from rho0
         v32, v64 = np.zeros((1, D)), np.zeros((1, D))
