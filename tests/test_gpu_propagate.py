@@ -380,6 +380,41 @@ def test_compact_columns_match_wide(G):
             assert np.array_equal(a, b), (var, prec, np.abs(a - b).max())
 
 
+def test_compact_columns_dropped_for_nonlocal_operators(G):
+    """A random sparse H0 at N = 260 couples pairs (j, k) to pairs far away in the basis (about
+    4 rows in 10 reach a column beyond 16383 of both the row and its S/J partner), so assembly
+    keeps Q1 folded but builds no 16-bit copy, and propagation gives the same states as with
+    GKSL_ASM_WIDE_COLUMNS."""
+    N = 260
+    D = N * N - 1
+    H0 = W.random_operator(N, 0.005, 41, hermitian=True)
+    H1 = W.CSR.from_dense(np.diag(np.linspace(-1.0, 1.0, N)).astype(complex))
+    outs = {}
+    for flags in (G.GKSL_ASM_FP32, G.GKSL_ASM_FP32 | G.GKSL_ASM_WIDE_COLUMNS):
+        ctx = G.gksl_create(N)
+        try:
+            G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 1.0, op=H0)
+            G.set_csr_operator(G.gksl_set_h1, ctx, op=H1)
+            G.gksl_set_drive(ctx, 0.5, 0.5, 1.0)
+            G.gksl_assemble(ctx, flags)
+            info = G.gksl_get_info(ctx)
+            assert info.q1_folded == 1
+            assert list(info.compact_columns) == [0, 0] and info.compact_escaped_rows == 0
+            spp = G.gksl_min_stable_steps(ctx)
+            rho0 = np.zeros((N, N))
+            rho0[0, 0] = 1.0
+            for prec in (64, 32):
+                G.gksl_set_rho0(ctx, rho0.copy())
+                outs[(flags, prec)] = run_gpu(G, ctx, spp, 40, 40, precision=prec, D=D)[0]
+                assert G.gksl_get_info(ctx).rk4_compact[0 if prec == 64 else 1] == 0
+        finally:
+            G.gksl_destroy(ctx)
+    for prec in (64, 32):
+        a, b = outs[(G.GKSL_ASM_FP32, prec)], outs[(G.GKSL_ASM_FP32 | G.GKSL_ASM_WIDE_COLUMNS, prec)]
+        assert np.isfinite(a).all() and np.abs(a).max() > 0
+        assert np.array_equal(a, b)
+
+
 def test_folded_q1_matches_separate_stream(G):
     """Q1 folded into the propagation format (the default for the dimer, whose H1 is diagonal)
     against Q1 as a separate stream (GKSL_ASM_NO_FOLD): the same RK4 map up to rounding, in
