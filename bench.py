@@ -123,6 +123,20 @@ def stage_bytes(nnz0, nnz1, D, precision, q1_folded=False, wide_entries=None):
     return (4 * mat + vec) / 4.0
 
 
+def stage_fp64_ops(nnz0, D, n_long, q1_folded):
+    """FP64 operations per FP64 stage launch, averaged over the 4 stages of a step: one FMA per
+    stored entry of [Q0 + E Q1 | K], one per short row for the folded Q1 value, 1.75 per row in
+    the stage updates (1, 2, 2, 2), and the 2 x 5 shuffle additions of the two warp sums of
+    each long row (32 lanes each)."""
+    return nnz0 + ((D - n_long) if q1_folded else 0) + 1.75 * D + 2 * 5 * 32 * n_long
+
+
+def fp64_peak_gops(sm_mhz):
+    """FP64 operations per second of GB300 at an SM clock: 152 SMs x 2 per clock (the nominal
+    1.25 TFLOP/s counts an FMA as 2 flops at the 2070 MHz maximum)."""
+    return 152 * 2 * sm_mhz * 1e6 / 1e9
+
+
 def wide_entries(info, p):
     """Entries read with int32 columns when the stage kernel in use for precision slot p reads
     the 16-bit columns (None: it reads int32 columns only): the long rows' entries and every
@@ -321,6 +335,13 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_launch,
                 "kernel": kernel + " (fused SpMV + RK4 stage update, FP64)"}
+    # the co-limit: the FP64 pipe, against its rate at the SM clock sampled in the timed region
+    ops = stage_fp64_ops(info.nnz_q0, D, info.long_rows, bool(info.q1_folded))
+    fp64_peak = fp64_peak_gops(ck["sm_mhz"] if ck else 2070.0)
+    gops = ops / (avg_launch_ms * 1e-3) / 1e9
+    roofline["fp64_pipe"] = {"ops_per_launch": ops, "achieved": gops, "peak": fp64_peak, "unit": "G FP64 ops/s",
+                             "frac": gops / fp64_peak,
+                             "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x sampled SM clock"}
 
     # end to end through the C ABI with pinned host buffers: H2D of v, propagate, D2H of v
     host_in = torch.empty(D, dtype=torch.float64, pin_memory=True)
