@@ -97,10 +97,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def code_text(src):
+    """Source text without comments and blank space, so that a comment edit keeps the hash."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def src_hash():
+    """Hash of the stage-kernel sources (code only) that keys the committed DRAM capture."""
     h = hashlib.sha256()
     for f in ("rk4.cu", "stage.cuh", "hyb.cu", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1812_11626_gb300", "csrc", f), "rb").read())
+        h.update(code_text(open(os.path.join(ROOT, "paper_1812_11626_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -8,7 +8,9 @@
 // The stage times are t_n, t_n + h/2 (twice), t_n + h with t_n = t0 + n h; the drive values
 // eps(t) - E = A sin(omega t) for a whole run are tabulated once per call, so no thread
 // evaluates a sine.  Matrix streams are loaded with the evict-first hint (__ldcs) so the
-// state-sized vectors stay in L2; the gather of y goes through the read-only path.
+// state-sized vectors stay in L2; the gather of y goes through the read-only path.  Columns come
+// from the 32-bit ELL array or, where the variant timer keeps it, from its 16-bit relative copy
+// (Hyb::ell_c16), whose escaped rows get threads of their own at the front of the grid.
 //
 // FP32 bulk form: the same kernels on FP32 values and vectors, with the FP32 increment
 // h/6 (acc + k4) added to an FP64 master state every step, and (optionally) one full FP64
