@@ -26,3 +26,48 @@ def test_reference_arm_prints_one_complete_json_line():
     e = j["e2e"]
     assert e["value"] == j["value"] and e["unit"] == j["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+class _Info:
+    """The gksl_info fields the bench's accounting reads, at the N = 1000 dimer's values."""
+    nnz_q0, nnz_q1, D, long_rows, tail_nnz, ell_width_q0 = 18449538, 999000, 999999, 994, 512396, 18
+    compact_escaped_rows, q1_folded = 2647, 1
+
+    def __init__(self, variants, compact):
+        self.rk4_variant, self.rk4_compact = variants, compact
+
+
+def test_stage_accounting_at_n1000():
+    """Algorithmic bytes and FP64 operations per stage launch at N = 1000, worked out by hand from
+    their definitions (12 B per stored entry + 8 B of folded Q1 value per row + 17 vector passes
+    of 8 B per step, averaged over 4 stages; 16-bit columns: 2 B less per entry, 2 B more per entry
+    read with a 32-bit column; FP32: 4-byte values and the FP64 master update)."""
+    b = _bench()
+    nnz0, nnz1, D = _Info.nnz_q0, _Info.nnz_q1, _Info.D
+    assert b.stage_bytes(nnz0, nnz1, D, 64, True) == 263394414
+    assert b.stage_bytes(nnz0, nnz1, D, 64, False) == 267382422
+    wide = _Info.tail_nnz + _Info.compact_escaped_rows * _Info.ell_width_q0
+    assert b.stage_bytes(nnz0, nnz1, D, 64, True, wide) == 227615422
+    assert b.stage_bytes(nnz0, nnz1, D, 32, True, wide) == 136817287
+    assert b.stage_bytes(nnz0, nnz1, D, 32, True) == 172596279
+    assert b.stage_fp64_ops(nnz0, D, _Info.long_rows, True) == 21516621.25
+    assert abs(b.fp64_peak_gops(2070.0) - 629.28) < 1e-9
+    info = _Info([0, 0], [0, 1])
+    assert b.wide_entries(info, 0) is None and b.wide_entries(info, 1) == wide
+    assert b.kernel_name(info, 0) == "k_stage64<S,18,true,false>"
+    assert b.kernel_name(info, 1) == "k_stage32<S,18,true,true>"
+    assert b.kernel_name(_Info([3, 2], [1, 0]), 0) == "k_stage_pdl<S,18,double,true,true>"
+    assert b.kernel_name(_Info([3, 2], [1, 0]), 1) == "k_stage_r2<S,18,float,true>"
+
+
+def test_source_hash_ignores_comments():
+    b = _bench()
+    code = "int f(int x) {\n    return x + 1;   // one more\n}\n/* block\n comment */\n"
+    assert b.code_text(code) == b.code_text("int f(int x) { return x + 1; }")
+    assert b.code_text(code) != b.code_text("int f(int x) { return x + 2; }")
