@@ -591,8 +591,8 @@ void assemble(gksl_ctx *c, unsigned flags) {
     c->q1_folded = !(flags & GKSL_ASM_NO_FOLD) &&
                    fold_q1(q0e, c->Q1, D, c->hyb0, fp32 ? &c->hyb0f : nullptr, c->q1v, c->q1vf, s);
     // 16-bit relative columns for the folded stage stream (built from the final slot order)
-    c->hyb0.ell_c16.release();
-    c->hyb0f.ell_c16.release();
+    drop_c16(c->hyb0);
+    drop_c16(c->hyb0f);
     if (c->q1_folded && !(flags & GKSL_ASM_WIDE_COLUMNS)) {
         build_c16(c->hyb0, c->P2, s);
         if (fp32) build_c16(c->hyb0f, c->P2, s);

@@ -265,11 +265,16 @@ __global__ void k_c16(const int *__restrict__ ell_col, long long ld, int W, long
 }  // namespace
 
 template <typename VT>
-bool build_c16(Hyb<VT> &h, long long pairs, cudaStream_t s) {
+void drop_c16(Hyb<VT> &h) {
     h.ell_c16.release();
     h.c16_esc.release();
-    h.c16_pairs = pairs;
     h.n_esc = 0;
+}
+
+template <typename VT>
+bool build_c16(Hyb<VT> &h, long long pairs, cudaStream_t s) {
+    drop_c16(h);
+    h.c16_pairs = pairs;
     if (h.width < 1 || h.rows < 1) return false;
     h.ell_c16.alloc((size_t)(h.ld * h.width));
     DBuf<long long> flag((size_t)h.rows), pos((size_t)h.rows + 1);
@@ -277,7 +282,7 @@ bool build_c16(Hyb<VT> &h, long long pairs, cudaStream_t s) {
     GK_LAUNCH_CHECK();
     const long long n = scan_ll(flag.p, pos.p, h.rows, true, true, s);
     if (n * 8 > h.rows - h.n_long) {
-        h.ell_c16.release();
+        drop_c16(h);
         return false;
     }
     h.n_esc = n;
@@ -290,6 +295,8 @@ bool build_c16(Hyb<VT> &h, long long pairs, cudaStream_t s) {
     return true;
 }
 
+template void drop_c16<double>(Hyb<double> &);
+template void drop_c16<float>(Hyb<float> &);
 template bool build_c16<double>(Hyb<double> &, long long, cudaStream_t);
 template bool build_c16<float>(Hyb<float> &, long long, cudaStream_t);
 

@@ -74,6 +74,8 @@ bool fold_q1(const CsrR &q0e, const CsrR &q1, long long rows, Hyb<double> &h0, H
 // N(N-1)/2 pairs; kept when at most one short row in eight falls back to 32-bit columns
 template <typename VT>
 bool build_c16(Hyb<VT> &h, long long pairs, cudaStream_t s);
+template <typename VT>
+void drop_c16(Hyb<VT> &h);   // release the 16-bit copy and its escape list
 // several matrices applied together (one long-row set; entries scaled by `scales`)
 void build_hyb_multi(const std::vector<const CsrR *> &ms, const std::vector<double> &scales, long long rows,
                      const std::vector<Hyb<double> *> &out, const std::vector<Hyb<float> *> &outf, cudaStream_t s);

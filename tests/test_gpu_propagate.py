@@ -370,6 +370,11 @@ def test_compact_columns_match_wide(G):
                 info = G.gksl_get_info(ctx)
                 assert all(info.rk4_variant_us[0][v] > 0 for v in range(4))
                 assert [info.rk4_variant_us_c16[0][v] > 0 for v in range(4)] == [True, True, False, True]
+                # reassembled with 32-bit columns only: the copy and its escape list are gone
+                G.gksl_assemble(ctx, flags | G.GKSL_ASM_WIDE_COLUMNS)
+                info2 = G.gksl_get_info(ctx)
+                assert list(info2.compact_columns) == [0, 0] and info2.compact_escaped_rows == 0
+                assert info2.device_bytes < info.device_bytes
         finally:
             G.gksl_destroy(ctx)
     assert np.array_equal(outs[(True, "0f", 64)], outs[(True, "0", 64)])
