@@ -34,7 +34,7 @@ namespace gk {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;   // largest block; small systems launch smaller ones (adj_grid)
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxCh = gksl_ctx::kMaxCh;
 
@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
 #pragma unroll
     for (int k = 0; k < NSLOT; ++k) g[k] = 0.0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nthr = blockDim.x, nwarp = nthr >> 5;
     double u[NC];
     // own-row part of the stage: the epilogue and the gradient partials of row r
     auto finish_row = [&](long long r, const double (&u)[NC]) {
@@ -191,14 +192,14 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
         adj_epilogue<STAGE, VT>(a, r, alpha * ysum, lam, lacc, kb_out, w, lam_out, beta);
     };
     if ((int)blockIdx.x < a.nb_long) {
-        for (long long i = (long long)blockIdx.x * kWarps + warp; i < a.n_long; i += (long long)a.nb_long * kWarps) {
+        for (long long i = (long long)blockIdx.x * nwarp + warp; i < a.n_long; i += (long long)a.nb_long * nwarp) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) u[c] = c < a.nch ? tail_row<VT>(a.ch[c], i, lane, x) : 0.0;
             if (lane == 0) finish_row(a.long_rows[i], u);
         }
     } else {
-        const long long stride = (long long)(gridDim.x - a.nb_long) * kThreads;
-        for (long long r = (long long)(blockIdx.x - a.nb_long) * kThreads + threadIdx.x; r < a.D; r += stride) {
+        const long long stride = (long long)(gridDim.x - a.nb_long) * nthr;
+        for (long long r = (long long)(blockIdx.x - a.nb_long) * nthr + threadIdx.x; r < a.D; r += stride) {
             if (__ldcs(a.ch[0].ell_col + r) < 0) continue;   // long row, handled by a warp above
 #pragma unroll
             for (int c = 0; c < NC; ++c) u[c] = c < a.nch ? ell_row<VT>(a.ch[c], r, x) : 0.0;
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
     if (threadIdx.x < NSLOT) {
         const int k = threadIdx.x;
         double sum = 0.0;
-        for (int ww = 0; ww < kWarps; ++ww) sum += red[ww][k];
+        for (int ww = 0; ww < nwarp; ++ww) sum += red[ww][k];
         double f = alpha;
         if (k == a.q1ch) f *= th;
         part[(long long)blockIdx.x * NSLOT + k] += f * sum;
@@ -230,17 +231,23 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
 }
 
 // blocks of one reverse stage: up to one per SM for the long rows (a warp each), then the ELL
-// rows (a thread each), both walked with a grid stride; at most four blocks per SM in all (the
-// register budget of the 4-channel kernel), so the whole grid is resident at once
+// rows (a thread each), both walked with a grid stride; at most 1024 threads per SM in all (the
+// register budget of the 4-channel kernel), so the whole grid is resident at once.  Blocks are
+// halved (down to 64 threads) while the rows would fill fewer than four blocks per SM, so that
+// a small system's rows spread evenly over every SM (N = 200: 64 threads, 4-15 % faster).
 struct AdjGrid {
     int nb_long;
     unsigned total;
+    int threads;
 };
 
 AdjGrid adj_grid(long long n_long, long long D, int sms) {
-    long long nl = std::min<long long>((n_long + kWarps - 1) / kWarps, sms);
-    long long ne = std::min<long long>((D + kThreads - 1) / kThreads, 4LL * sms - nl);
-    return AdjGrid{(int)nl, (unsigned)(nl + std::max(1LL, ne))};
+    int bt = kThreads;
+    while (bt > 64 && (D + bt - 1) / bt < 4LL * sms) bt /= 2;
+    const long long per_sm = 1024 / bt, wpb = bt / 32;
+    long long nl = std::min<long long>((n_long + wpb - 1) / wpb, sms);
+    long long ne = std::min<long long>((D + bt - 1) / bt, per_sm * sms - nl);
+    return AdjGrid{(int)nl, (unsigned)(nl + std::max(1LL, ne)), bt};
 }
 
 __global__ void k_fill_scaled(double *__restrict__ y, const double *__restrict__ x, double a, long long n) {
@@ -316,22 +323,22 @@ struct ExecSet {
 
 // the four reverse stages of one step: kb4 from lam', then kb3, kb2, and lam from kb1
 template <typename VT, int NC>
-void rev_stages_t(const AdjArgs<VT> &a, unsigned grid, cudaStream_t s, const VT *lam_in, const VT *Y1, const VT *Y2,
+void rev_stages_t(const AdjArgs<VT> &a, unsigned grid, int bt, cudaStream_t s, const VT *lam_in, const VT *Y1, const VT *Y2,
                   const VT *Y3, const VT *Y4, VT *ka, VT *kb, double *lam, double *lacc, const double *w,
                   double *part) {
-    k_adjoint<4, VT, NC><<<grid, kThreads, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
-    k_adjoint<3, VT, NC><<<grid, kThreads, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
-    k_adjoint<2, VT, NC><<<grid, kThreads, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
-    k_adjoint<1, VT, NC><<<grid, kThreads, 0, s>>>(a, ka, Y1, lam, lacc, nullptr, w, lam, part);
+    k_adjoint<4, VT, NC><<<grid, bt, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
+    k_adjoint<3, VT, NC><<<grid, bt, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
+    k_adjoint<2, VT, NC><<<grid, bt, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
+    k_adjoint<1, VT, NC><<<grid, bt, 0, s>>>(a, ka, Y1, lam, lacc, nullptr, w, lam, part);
 }
 
 // the four reverse stages of one step: kb4 from lam', then kb3, kb2, and lam from kb1
 template <typename VT>
-void rev_stages(const AdjArgs<VT> &a, int NC, unsigned grid, cudaStream_t s, const VT *lam_in, const VT *Y1,
+void rev_stages(const AdjArgs<VT> &a, int NC, unsigned grid, int bt, cudaStream_t s, const VT *lam_in, const VT *Y1,
                 const VT *Y2, const VT *Y3, const VT *Y4, VT *ka, VT *kb, double *lam, double *lacc, const double *w,
                 double *part) {
-    if (NC == 4) rev_stages_t<VT, 4>(a, grid, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part);
-    else rev_stages_t<VT, kMaxCh>(a, grid, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part);
+    if (NC == 4) rev_stages_t<VT, 4>(a, grid, bt, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part);
+    else rev_stages_t<VT, kMaxCh>(a, grid, bt, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part);
 }
 
 }  // namespace
@@ -464,14 +471,14 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
             const float *Y1 = (const float *)Yp(0, i), *Y2 = (const float *)Yp(1, i), *Y3 = (const float *)Yp(2, i),
                         *Y4 = (const float *)Yp(3, i);
             float *ka = (float *)kbA.p, *kb = (float *)kbB.p;
-            rev_stages<float>(a, NC, grid, s, lamf.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p, part.p);
+            rev_stages<float>(a, NC, grid, ag.threads, s, lamf.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p, part.p);
         } else {
             AdjArgs<double> a = a64;
             a.local = i;
             const double *Y1 = (const double *)Yp(0, i), *Y2 = (const double *)Yp(1, i),
                          *Y3 = (const double *)Yp(2, i), *Y4 = (const double *)Yp(3, i);
             double *ka = (double *)kbA.p, *kb = (double *)kbB.p;
-            rev_stages<double>(a, NC, grid, s, lam.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p, part.p);
+            rev_stages<double>(a, NC, grid, ag.threads, s, lam.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p, part.p);
         }
         GK_LAUNCH_CHECK();
     };
