@@ -141,9 +141,10 @@ gksl_status gksl_structure_enumerate(int N, int which, long long capacity, int *
  * generator of the same pair (j, k) in the other half of the basis); rows with a column beyond
  * +-16383 of both get threads of their own that read the 32-bit columns, and the long rows keep
  * their warps.  The copy is dropped when more than one short row in eight would escape.  The
- * first propagation times the stage kernels with either column width and keeps the fastest
- * (gksl_info.rk4_compact); both compute the same map with the same arithmetic (bit-identical
- * results). */
+ * first propagation in each precision times the stage kernels with either column width and keeps
+ * the 16-bit columns only when they are at least 2 % faster (gksl_info.rk4_compact; the
+ * environment variable GKSL_RK4_COLUMNS=32 skips them).  Both compute the same map with the same
+ * arithmetic (bit-identical results). */
 #define GKSL_ASM_WIDE_COLUMNS 32u
 /* Matrix-free form: build no CSR matrix; keep H0 (+ E H1), H1, Gamma = 1/2 sum_p gamma_p L_p^+ L_p
  * and sqrt(gamma_p) L_p as complex diagonals (O(N) data) and let gksl_propagate apply Q(t) v + K on
