@@ -71,3 +71,21 @@ def test_source_hash_ignores_comments():
     code = "int f(int x) {\n    return x + 1;   // one more\n}\n/* block\n comment */\n"
     assert b.code_text(code) == b.code_text("int f(int x) { return x + 1; }")
     assert b.code_text(code) != b.code_text("int f(int x) { return x + 2; }")
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    """Launched as the multi-GPU runs are (torch.distributed.run, two ranks), the reference arm
+    runs on rank 0 alone: one JSON line with n_gpus = 2, and every rank exits 0."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"],
+                       capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference" and j["n_gpus"] == 2 and j["value"] > 0
