@@ -110,3 +110,21 @@ def expand_sparse(X):
         c = 1.0 / np.sqrt(l * (l + 1.0))
         out[2 * P2 + l - 1] = c * (d[:l].sum() - l * d[l])
     return out
+
+
+def expand_dense(X):
+    """Tr(F_s X) for a dense N x N array X, the entry formulas of ``expand_sparse`` on whole arrays.
+
+    S^(j,k): (X_jk + X_kj)/sqrt2 and J^(j,k): i (X_jk - X_kj)/sqrt2 over the pairs j < k in
+    lexicographic order (numpy's upper-triangle order is row-major, the same order);
+    D^l: c_l (sum_{k<l} X_kk - l X_ll) from a running sum of the diagonal.
+    """
+    X = np.asarray(X, dtype=np.complex128)
+    N = X.shape[0]
+    j, k = np.triu_indices(N, 1)
+    up, lo = X[j, k], X[k, j]
+    d = np.diag(X)
+    l = np.arange(1, N)
+    below = np.cumsum(d)[:-1]                      # sum_{k<l} X_kk for l = 1..N-1
+    dpart = (below - l * d[1:]) / np.sqrt(l * (l + 1.0))
+    return np.concatenate([(up + lo) / np.sqrt(2.0), 1j * (up - lo) / np.sqrt(2.0), dpart])

@@ -47,10 +47,11 @@ def initial_v(d):
     return _b.expand_sparse(rho0).real
 
 
-def propagate_dimer(d, u, steps_per_period, nsteps, emit_every=None, v0=None, t0=0.0, drive="sin"):
+def propagate_dimer(d, u, steps_per_period, nsteps, emit_every=None, v0=None, t0=0.0, drive="sin", threaded=False):
     """RK4 of the dimer from v0 (default v(0)); returns (v_final, emitted list).
 
-    drive: "sin" (theta = sin(omega t)) or "square" (theta = +-1, Sec. III driving (i))."""
+    drive: "sin" (theta = sin(omega t)) or "square" (theta = +-1, Sec. III driving (i)).
+    threaded: run the same map with the C RK4 on every host core (``native.rk4``)."""
     p = d.params
     T = 2 * np.pi / p["omega"]
     h = T / steps_per_period
@@ -58,6 +59,9 @@ def propagate_dimer(d, u, steps_per_period, nsteps, emit_every=None, v0=None, t0
     K = d.rate * u.K1
     if v0 is None:
         v0 = initial_v(d)
+    if threaded:
+        return native.rk4(Q0, u.Q1, K, p["E"], p["A"], p["omega"], v0, h, nsteps, t0=t0, emit_every=emit_every,
+                          drive=drive)
     step = _p.eps_square_step(p["E"], p["A"], p["omega"]) if drive == "square" else None
     return _p.rk4(Q0, u.Q1, K, _p.eps_fn(p["E"], p["A"], p["omega"]), v0, h, nsteps, t0=t0,
                   emit_every=emit_every, eps_step=step)

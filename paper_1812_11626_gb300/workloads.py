@@ -184,3 +184,17 @@ def random_banded(N, half_bandwidth, seed, hermitian=False, real=False):
     if hermitian:
         X = X + X.conj().T
     return CSR.from_dense(X)
+
+
+def random_density_matrix(N, rank, seed):
+    """Seeded dense density matrix rho = X X^+ / Tr(X X^+), X an N x rank complex Gaussian draw.
+
+    Every entry of rho is nonzero (almost surely), so every row of the unfolded system sees a
+    nonzero input; Hermitian, unit trace, positive semidefinite of the given rank.
+    Returns (re, im) as two dense float64 arrays."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((N, rank)) + 1j * rng.standard_normal((N, rank))
+    rho = X @ X.conj().T
+    rho /= np.trace(rho).real
+    rho = 0.5 * (rho + rho.conj().T)
+    return np.ascontiguousarray(rho.real), np.ascontiguousarray(rho.imag)

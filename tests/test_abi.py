@@ -85,3 +85,27 @@ def test_info_struct_layout_matches_header(G, tmp_path):
     assert int(out["size"]) == ctypes.sizeof(G.gksl_info)
     for f in fields:
         assert int(out[f]) == getattr(G.gksl_info, f).offset, f
+
+
+def test_noalloc_arguments_rejected_before_any_call(G):
+    """The allocation-free entry point: the binding rejects host tensors and wrong dtypes before it
+    calls the library, and the library itself rejects an oversized D or a null A0 with
+    GKSL_ERR_ARG before it touches the GPU."""
+    import ctypes
+
+    import torch
+    D = 3
+    rp = torch.tensor([0, 1, 2, 3], dtype=torch.int32)
+    col = torch.tensor([0, 1, 2], dtype=torch.int32)
+    val = torch.ones(3, dtype=torch.float64)
+    v = torch.zeros(D, dtype=torch.float64)
+    for args in ((D, rp, col, val, None, None, None, None, v),
+                 (D, rp.long(), col, val, None, None, None, None, v)):
+        with pytest.raises(G.GkslError) as e:
+            G.gksl_propagate_csr_noalloc(*args, 0.0, 1e-3, 1, 0.0, 0.0, 1.0)
+        assert e.value.status == G.GKSL_ERR_ARG
+    f = G._lib.gksl_propagate_csr_noalloc
+    one = ctypes.c_void_p(8)   # never dereferenced: both calls return before any CUDA call
+    assert f(G.GKSL_NOALLOC_MAX_D + 1, one, one, one, None, None, None, None, one, 0.0, 1e-3, 1, 0.0, 0.0, 1.0,
+             None) == G.GKSL_ERR_ARG
+    assert f(D, None, None, None, None, None, None, None, one, 0.0, 1e-3, 1, 0.0, 0.0, 1.0, None) == G.GKSL_ERR_ARG

@@ -411,3 +411,128 @@ def test_adjoint_matches_complex_step():
         thm = dict(theta); thm[key] = theta[key] - hfd
         fd = (loss(thp).real - loss(thm).real) / (2 * hfd)
         assert abs(fd - cs) <= 1e-6 * max(1.0, abs(cs))
+
+
+# ------------------------------------------------------------- dense expansion, threaded RK4
+
+@pytest.mark.parametrize("N", [2, 3, 5, 7])
+def test_expand_dense_reads_unit_vectors_off_the_generators(N):
+    """Orthonormality (Sec. II, Tr(F_i F_k) = delta_ik): the coefficients of generator F_s are the
+    unit vector e_s; on random complex matrices the entry formulas equal the trace definition."""
+    labs = B.labels(N)
+    for s, lab in enumerate(labs):
+        x = B.expand_dense(B.generator(N, lab))
+        e = np.zeros(len(labs))
+        e[s] = 1.0
+        assert np.abs(x - e).max() < 1e-15
+    rng = np.random.default_rng(N)
+    X = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    assert np.abs(B.expand_dense(X) - B.expand(X)).max() < 1e-14
+
+
+def test_expand_dense_parseval_at_n1000():
+    """Eq. 6 with an orthonormal basis: |v|^2 = Tr rho^2 - 1/N for a dense rank-3 state at N = 1000,
+    and every coefficient of that state is nonzero."""
+    re, im = W.random_density_matrix(1000, 3, 7)
+    rho = re + 1j * im
+    v = B.expand_dense(rho)
+    assert np.abs(v.imag).max() == 0.0
+    assert abs(v.real @ v.real - (np.vdot(rho, rho).real - 1e-3)) < 1e-12
+    assert np.abs(v.real).min() > 0
+
+
+def test_c_rk4_pair_rotation_and_fourth_order():
+    """The threaded C RK4 (native.rk4) against closed forms, not against the Python RK4: the driven
+    pair rotation of a diagonal H (J = 0, gamma = 0) and fourth-order convergence to exp(tL)."""
+    N = 5
+    e = np.array([0.0, 0.7, 1.1, 2.0, 2.2])
+    o = np.array([-2.0, -1.0, 0.0, 1.0, 2.0])
+    E, A, w = 0.3, 0.8, 1.7
+    F = B.basis(N)
+    Q0, _ = Lb.unfold_dense(np.diag(e).astype(complex), (), (), F)
+    Q1, _ = Lb.unfold_dense(np.diag(o).astype(complex), (), (), F)
+    rng = np.random.default_rng(2)
+    X = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    rho0 = X @ X.conj().T
+    rho0 /= np.trace(rho0)
+    t, n = 3.0, 3000
+    v, out = native.rk4(Q0, Q1, None, E, A, w, B.expand(rho0).real, t / n, n, emit_every=1000)
+    phi = np.subtract.outer(e, e) * t + np.subtract.outer(o, o) * (E * t + A * (1 - np.cos(w * t)) / w)
+    assert np.abs(B.rho_from_v(v, F) - rho0 * np.exp(-1j * phi)).max() < 1e-9
+    assert len(out) == 3 and np.array_equal(out[-1], v)
+    H0, _, L = _small_driven(3, seed=9)
+    F3 = B.basis(3)
+    Q, K = Lb.unfold_dense(H0, [L], [0.5], F3)
+    r0 = np.diag([1.0, 0, 0]).astype(complex)
+    exact = B.expand(P.rho_expm(H0, [L], [0.5], r0, 2.0)).real
+    errs = [np.abs(native.rk4(Q, None, K, 0.0, 0.0, 1.0, B.expand(r0).real, 2.0 / n, n)[0] - exact).max()
+            for n in (50, 100, 200)]
+    assert 13 < errs[0] / errs[1] < 19 and 13 < errs[1] / errs[2] < 19, errs
+
+
+@pytest.mark.parametrize("drive", ["sin", "square"])
+def test_c_rk4_equals_python_rk4_on_the_dimer(drive):
+    """Both oracle RK4s run the same map: N = 10 dimer, 3 periods, emitted states at period ends."""
+    d = W.dimer(10)
+    u = SYS.unfold_dimer(d)
+    a, ea = SYS.propagate_dimer(d, u, 200, 600, emit_every=200, drive=drive)
+    b, eb = SYS.propagate_dimer(d, u, 200, 600, emit_every=200, drive=drive, threaded=True)
+    assert len(ea) == len(eb) == 3
+    assert np.abs(a - b).max() < 1e-13 and max(np.abs(x - y).max() for x, y in zip(ea, eb)) < 1e-13
+
+
+# ------------------------------------------------------------- the loss window (reading O)
+
+def _rk4_factor(z):
+    """RK4's stability function: one step of y' = lam y multiplies y by R(h lam)."""
+    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+def test_loss_window_and_trapezoid_weights_closed_form():
+    """Diagonal H, no drive, no dissipator: rho_jk evolves by rho_jk' = -i (e_j - e_k) rho_jk, so RK4
+    multiplies it by r = R(-i (e_j - e_k) h) every step and the S^(j,k) component is
+    sqrt2 Re(rho_jk(0) r^n).  The trapezoid mean over the S + 1 grid points of period P,
+    n = (P-1) S .. P S, is then a geometric sum in closed form:
+        sqrt2 Re( rho_jk(0) r^((P-1) S) [ (1 - r^(S+1)) / (1 - r) - (1 + r^S) / 2 ] / S ).
+    A window shifted by one step, uniform weights or a wrong normalisation all miss it."""
+    N = 4
+    e = np.array([0.0, 0.9, 1.4, 2.35])
+    F = B.basis(N)
+    Q0, K = Lb.unfold_dense(np.diag(e).astype(complex), (), (), F)
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    rho0 = X @ X.conj().T
+    rho0 /= np.trace(rho0)
+    v0 = B.expand(rho0).real
+    S, period = 40, 3
+    h = 2 * np.pi / S
+    zero = np.zeros_like(Q0)
+    for (j, k) in ((0, 1), (1, 3)):
+        w = np.zeros(N * N - 1)
+        w[B.pair_index(N, j, k)] = 1.0
+        r = _rk4_factor(-1j * (e[j] - e[k]) * h)
+        geo = (1 - r ** (S + 1)) / (1 - r) - 0.5 * (1 + r ** S)
+        exact = np.sqrt(2) * (rho0[j, k] * r ** ((period - 1) * S) * geo / S).real
+        got = P.timeavg_loss(Q0, zero, K, lambda t: 0.0, v0, w, 0.0, h, S, period)
+        assert abs(got - exact) < 1e-13, (j, k, got, exact)
+        # the same window through the adjoint's forward sweep
+        L, _ = P.timeavg_adjoint(Q0, zero, K, lambda t: 0.0, v0, w, 0.0, h, S, period, [None], [None], [None])
+        assert abs(L - exact) < 1e-13
+        # a window one step late is measurably different (so the pin can fail)
+        late = np.sqrt(2) * (rho0[j, k] * r ** ((period - 1) * S + 1) * geo / S).real
+        assert abs(late - exact) > 1e-4
+
+
+def test_loss_of_a_constant_observable_is_the_constant():
+    """O = c 1: <O> = c Tr rho = c at every time, so the period mean is c for any window and state
+    (the trapezoid weights sum to one)."""
+    d = W.dimer(6)
+    u = SYS.unfold_dimer(d)
+    p = d.params
+    Q0 = u.q0(p["J"], p["U"], d.rate)
+    for S, period in ((30, 1), (25, 2)):
+        w, c0 = P.observable_weights(np.full(6, 2.5))
+        assert np.abs(w).max() < 1e-15 and abs(c0 - 2.5) < 1e-15
+        L = P.timeavg_loss(Q0, u.Q1, d.rate * u.K1, P.eps_fn(p["E"], p["A"], p["omega"]), SYS.initial_v(d), w, c0,
+                           2 * np.pi / S, S, period)
+        assert abs(L - 2.5) < 1e-13
