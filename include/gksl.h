@@ -264,11 +264,15 @@ gksl_status gksl_batch_info(gksl_batch *b, int group, int *instances_per_lane, d
  * float64, device) is updated in place.  Everything is caller-owned and nothing is copied or
  * allocated: the RK4 work vectors live in a fixed array compiled into the library (3 x
  * GKSL_NOALLOC_MAX_D float64 per GPU, held until the process exits).  The first call on each
- * device looks the array's address up (cudaGetSymbolAddress) with that device current, so make
- * the first call before any stream capture.  Calls whose work overlaps on the GPU share the
- * array and race.  Returns GKSL_ERR_ARG for D > GKSL_NOALLOC_MAX_D or a null pointer,
- * GKSL_ERR_CUDA if a launch fails; work is enqueued on cuda_stream (NULL: legacy default stream)
- * and the call does not synchronise. */
+ * device looks the array's address up (cudaGetSymbolAddress) with that device current and keeps
+ * it for the life of the process, so make the first call before any stream capture, and do not
+ * call this again on a device after cudaDeviceReset.  Calls whose work overlaps on the GPU share
+ * the array and race.  The kernels index the arrays without checks: rowptr must run from 0 to at
+ * most the length of col/val, columns must lie in [0, D), and every array must be on the current
+ * device.  Returns GKSL_ERR_ARG for D > GKSL_NOALLOC_MAX_D, a null pointer, h <= 0 or
+ * n_steps < 0; GKSL_ERR_CUDA when a CUDA error is already pending at entry (nothing is launched
+ * and that error is left for its owner) or a launch fails.  Work is enqueued on cuda_stream
+ * (NULL: legacy default stream) and the call does not synchronise. */
 gksl_status gksl_propagate_csr_noalloc(long long D, const int *a0_rowptr, const int *a0_col, const double *a0_val,
                                        const int *a1_rowptr, const int *a1_col, const double *a1_val,
                                        const double *K, double *v, double t0, double h, long long n_steps, double E,

@@ -11,10 +11,15 @@
 // (3 x GKSL_NOALLOC_MAX_D doubles, 6 MiB) until the process exits, and every call on that GPU
 // shares it.  Host code cannot use the array's name as a device address, so the first call on
 // each device looks the address up with cudaGetSymbolAddress (with that device current) and
-// keeps it; that first call should therefore happen before any stream capture.  Calls whose
-// kernels overlap on the GPU (two streams, or two host threads) race on the array.  Nothing in
-// the array needs to start at zero: every element a stage reads was written earlier in the same
-// step.
+// keeps it for the life of the process; that first call should therefore happen before any
+// stream capture.  After cudaDeviceReset the kept address no longer names the array, so this
+// entry point must not be called again on a device that has been reset.  Calls whose kernels
+// overlap on the GPU (two streams, or two host threads) race on the array.  Nothing in the array
+// needs to start at zero: every element a stage reads was written earlier in the same step.
+//
+// Errors: a CUDA error already pending when the call starts (left by other work) is reported as
+// GKSL_ERR_CUDA without launching anything and is left for its owner to read; a failed launch of
+// this call is cleared and reported as GKSL_ERR_CUDA.
 #include <cmath>
 #include <mutex>
 
@@ -61,13 +66,15 @@ __global__ void __launch_bounds__(kThreads) k_stage_csr(long long D, Csr a0, Csr
     if (STAGE == 4) { v[r] = v[r] + h6 * (acc[r] + k); }
 }
 
-// Device address of the work array on the current device, looked up once per device.
+// Device address of the work array on the current device, looked up once per device.  Called
+// with no error pending, so an error raised here is this call's own and is cleared.
 gksl_status work_address(double **out) {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return GKSL_ERR_CUDA;
     }
+    if (dev < 0 || dev >= kMaxDevices) return GKSL_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_work_addr[dev]) {
         void *p = nullptr;
@@ -91,6 +98,7 @@ extern "C" gksl_status gksl_propagate_csr_noalloc(long long D, const int *a0_row
     if (D < 1 || D > kMaxD) return GKSL_ERR_ARG;   // larger systems do not fit the fixed work array
     if (!a0_rowptr || !a0_col || !a0_val || !v || n_steps < 0 || !(h > 0.0)) return GKSL_ERR_ARG;
     if (a1_rowptr && (!a1_col || !a1_val)) return GKSL_ERR_ARG;
+    if (cudaPeekAtLastError() != cudaSuccess) return GKSL_ERR_CUDA;   // not ours: leave it pending
     double *work = nullptr;
     gksl_status st = work_address(&work);
     if (st != GKSL_OK) return st;
@@ -105,8 +113,11 @@ extern "C" gksl_status gksl_propagate_csr_noalloc(long long D, const int *a0_row
         const double e2 = E + A * std::sin(omega * (tn + 0.5 * h));
         const double e4 = E + A * std::sin(omega * (tn + h));
         k_stage_csr<1><<<grid, kThreads, 0, s>>>(D, m0, m1, K, e1, v, v, ya, acc, h, h2, h6);
+        if (cudaGetLastError() != cudaSuccess) return GKSL_ERR_CUDA;
         k_stage_csr<2><<<grid, kThreads, 0, s>>>(D, m0, m1, K, e2, ya, v, yb, acc, h, h2, h6);
+        if (cudaGetLastError() != cudaSuccess) return GKSL_ERR_CUDA;
         k_stage_csr<3><<<grid, kThreads, 0, s>>>(D, m0, m1, K, e2, yb, v, ya, acc, h, h2, h6);
+        if (cudaGetLastError() != cudaSuccess) return GKSL_ERR_CUDA;
         k_stage_csr<4><<<grid, kThreads, 0, s>>>(D, m0, m1, K, e4, ya, v, nullptr, acc, h, h2, h6);
         if (cudaGetLastError() != cudaSuccess) return GKSL_ERR_CUDA;
     }

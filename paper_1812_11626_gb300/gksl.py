@@ -323,17 +323,69 @@ def gksl_get_info(ctx):
 GKSL_NOALLOC_MAX_D = 262144
 
 
+def _noalloc_check(D, mats, K, v):
+    """Reject, before anything is launched, arguments the allocation-free kernels would index out
+    of bounds: every array a contiguous CUDA tensor on v's device, CSR rowptr/col int32 and values
+    float64, rowptr of D + 1 entries from 0 to at most the length of col and val, K and v float64
+    of D entries.  Reads the first and last rowptr entry of each matrix (two 4-byte copies)."""
+    import torch
+
+    def bad(msg):
+        raise GkslError(GKSL_ERR_ARG, f"gksl_propagate_csr_noalloc: {msg}")
+
+    if not isinstance(v, torch.Tensor) or not v.is_cuda:
+        bad("v must be a CUDA tensor")
+    dev = v.device
+
+    def tensor(name, x, dtype, n=None):
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            bad(f"{name} must be a CUDA tensor")
+        if x.device != dev:
+            bad(f"{name} is on {x.device}, v on {dev}")
+        if x.dtype != dtype:
+            bad(f"{name} must be {dtype}, got {x.dtype}")
+        if not x.is_contiguous():
+            bad(f"{name} must be contiguous")
+        if n is not None and x.numel() != n:
+            bad(f"{name} has {x.numel()} entries, expected {n}")
+
+    if not 1 <= int(D) <= GKSL_NOALLOC_MAX_D:
+        bad(f"D = {int(D)} must be in [1, GKSL_NOALLOC_MAX_D = {GKSL_NOALLOC_MAX_D}]")
+    tensor("v", v, torch.float64, int(D))
+    if K is not None:
+        tensor("K", K, torch.float64, int(D))
+    for name, (rp, col, val) in mats.items():
+        if rp is None and col is None and val is None and name == "A1":
+            continue
+        if rp is None or col is None or val is None:
+            bad(f"{name}: rowptr, col and val must all be given" + (" or all be None" if name == "A1" else ""))
+        tensor(f"{name} rowptr", rp, torch.int32, int(D) + 1)
+        tensor(f"{name} col", col, torch.int32)
+        tensor(f"{name} val", val, torch.float64, col.numel())
+        first, last = int(rp[0]), int(rp[-1])
+        if first != 0 or last > col.numel():
+            bad(f"{name} rowptr must run from 0 to at most {col.numel()} (got {first} .. {last})")
+
+
 def gksl_propagate_csr_noalloc(D, a0_rowptr, a0_col, a0_val, a1_rowptr, a1_col, a1_val, K, v, t0, h, n_steps, E, A,
                                omega, cuda_stream=None):
-    """Allocation-free RK4 on caller-owned device arrays (all array arguments are CUDA tensors)."""
-    st = _lib.gksl_propagate_csr_noalloc(int(D), _ptr(a0_rowptr), _ptr(a0_col), _ptr(a0_val), _ptr(a1_rowptr),
-                                         _ptr(a1_col), _ptr(a1_val), _ptr(K), _ptr(v), float(t0), float(h),
-                                         int(n_steps), float(E), float(A), float(omega), cuda_stream)
+    """Allocation-free RK4 on caller-owned device arrays (all array arguments CUDA tensors on one
+    device; the A1 triple and K may be None).  The arguments are checked first (``_noalloc_check``);
+    the call then runs with v's device current, on ``cuda_stream`` or, when that is None, on torch's
+    current stream of that device, so it is ordered after the work that produced its inputs."""
+    import torch
+    _noalloc_check(D, {"A0": (a0_rowptr, a0_col, a0_val), "A1": (a1_rowptr, a1_col, a1_val)}, K, v)
+    with torch.cuda.device(v.device):
+        if cuda_stream is None:
+            cuda_stream = torch.cuda.current_stream(v.device).cuda_stream
+        st = _lib.gksl_propagate_csr_noalloc(int(D), _ptr(a0_rowptr), _ptr(a0_col), _ptr(a0_val), _ptr(a1_rowptr),
+                                             _ptr(a1_col), _ptr(a1_val), _ptr(K), _ptr(v), float(t0), float(h),
+                                             int(n_steps), float(E), float(A), float(omega), cuda_stream)
     if st == GKSL_ERR_ARG:
-        raise GkslError(st, f"gksl_propagate_csr_noalloc: D = {int(D)} must be in [1, GKSL_NOALLOC_MAX_D = "
-                            f"{GKSL_NOALLOC_MAX_D}], h > 0, n_steps >= 0 and the A0, v pointers non-null")
+        raise GkslError(st, "gksl_propagate_csr_noalloc: h must be > 0 and n_steps >= 0")
     if st != GKSL_OK:
-        raise GkslError(st, f"gksl_propagate_csr_noalloc failed with status {st} (a CUDA launch failed)")
+        raise GkslError(st, f"gksl_propagate_csr_noalloc failed with status {st} (a CUDA error was pending or a "
+                            f"launch failed)")
 
 
 # ------------------------------------------------------------------ conveniences over the calls
