@@ -32,7 +32,7 @@ def oracle_grad(d, S, period):
                               dK=[None, u.K1, None, None])
 
 
-@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 2e-3)])
+@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
 def test_adjoint_vs_oracle(G, precision, tol, record):
     d = W.dimer(6)
     S, period = 60, 3
@@ -125,7 +125,7 @@ def test_adjoint_workload_period20_vs_finite_differences(G, record):
     the forward loss; its gradient with respect to (A, gamma, J, U) matches central differences
     (h = 1e-6 relative) of that forward loss, computed from every grid point of period 20 emitted
     to device memory and reduced by the library's observable kernel; the FP32 adjoint stays
-    within 1e-2 of each FP64 component (plus 1e-6 of the largest)."""
+    within 1e-4 of each FP64 component (plus 1e-6 of the largest)."""
     import torch
     d = W.dimer(200)
     P = 20
@@ -177,7 +177,7 @@ def test_adjoint_workload_period20_vs_finite_differences(G, record):
             record(f"grad_{key}_rel_diff_vs_central_differences", abs(fd - grad[i]) / abs(grad[i]))
             assert abs(fd - grad[i]) <= bound, (key, fd, grad[i], bound)
         record("fp32_grad_max_rel_diff_vs_fp64", np.max(np.abs(grad32 - grad) / np.abs(grad)))
-        assert np.all(np.abs(grad32 - grad) <= 1e-2 * np.abs(grad) + 1e-6 * gmax), (grad32, grad)
+        assert np.all(np.abs(grad32 - grad) <= 1e-4 * np.abs(grad) + 1e-6 * gmax), (grad32, grad)
     finally:
         G.gksl_destroy(ctx)
 
@@ -200,8 +200,8 @@ def test_autograd_function(G):
         G.gksl_destroy(ctx)
 
 
-@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 2e-3)])
-def test_adjoint_ragged_segments_vs_oracle(G, precision, tol):
+@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
+def test_adjoint_ragged_segments_vs_oracle(G, precision, tol, record):
     """S = 66 steps per period: the reverse sweep's checkpoint segments do not divide S, so the
     last segment of every period is shorter than the others."""
     d = W.dimer(5)
@@ -211,6 +211,7 @@ def test_adjoint_ragged_segments_vs_oracle(G, precision, tol):
         grad = np.zeros(4)
         loss = G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, period, precision, grad)
         L, g = oracle_grad(d, S, period)
+        record("grad_max_abs_diff_vs_oracle_over_max", np.abs(grad - g).max() / np.abs(g).max())
         assert abs(loss - L) < (1e-11 if precision == 64 else 1e-4)
         assert np.abs(grad - g).max() < tol * np.abs(g).max(), (grad, g)
         # a second call on the same context gives the same result bit for bit
@@ -221,8 +222,8 @@ def test_adjoint_ragged_segments_vs_oracle(G, precision, tol):
         G.gksl_destroy(ctx)
 
 
-@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 2e-3)])
-def test_adjoint_general_operators_vs_oracle(G, precision, tol):
+@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
+def test_adjoint_general_operators_vs_oracle(G, precision, tol, record):
     """Three H0 components, a drive operator and two dissipators (six gradient channels, more
     than the four-channel kernel holds), with gaps in the component and channel indices; the
     oracle side unfolds each operator by the definition Tr(F_s L(F_m)) on dense matrices."""
@@ -268,5 +269,6 @@ def test_adjoint_general_operators_vs_oracle(G, precision, tol):
     L_ref, g_ref = OP.timeavg_adjoint(Q0, Q1, K, OP.eps_fn(E, A, omega), v0, w, c0, h, S, period,
                                       dQ0=[None, RK[0][0], RK[1][0]] + Qk, dQ1=[(Q1, sinw)] + [None] * 5,
                                       dK=[None, RK[0][1], RK[1][1]] + [None] * 3)
+    record("grad_max_abs_diff_vs_oracle_over_max", np.abs(grad - g_ref).max() / np.abs(g_ref).max())
     assert abs(loss - L_ref) < (1e-11 if precision == 64 else 1e-4) * max(1.0, abs(L_ref))
     assert np.abs(grad - g_ref).max() < tol * np.abs(g_ref).max(), (grad, g_ref)
