@@ -84,11 +84,15 @@ gksl_status gksl_set_h1(gksl_ctx *ctx, const int *rowptr, const int *col, const 
 gksl_status gksl_set_dissipator(gksl_ctx *ctx, int p, double gamma_p, const int *rowptr, const int *col,
                                 const double *re, const double *im, int nnz);
 /* Dissipator given as a Kossakowski matrix A over the generators (Eq. 8): D x D row-major real and
- * imaginary parts (a_im may be NULL), Hermitian and positive semidefinite, rank <= GKSL_MAX_P,
- * N <= 64.  A is factorised as sum_p c_p c_p^+ (pivoted Cholesky; pivots <= tol * max diag(A) end
- * the factorisation) and channel p is set to L_p = sum_j c_pj F_j / |c_p| with gamma_p = |c_p|^2,
- * replacing every previously set channel.  GKSL_ERR_ARG if A is not Hermitian, not positive
- * semidefinite, or of higher rank. */
+ * imaginary parts (a_im may be NULL), Hermitian and positive semidefinite; replaces every
+ * previously set channel.  A is first factorised as sum_p c_p c_p^+ (pivoted Cholesky, pivots
+ * <= tol * max diag(A) end it): when at most GKSL_MAX_P pivots exhaust it and N <= 64, channel p
+ * is set to L_p = sum_j c_pj F_j / |c_p| with gamma_p = |c_p|^2 (GKSL_ERR_ARG if A is not
+ * positive semidefinite).  Otherwise (higher rank, or N > 64) A itself is kept on the device and
+ * channel 0 holds the whole Eq. 8 dissipator at gamma_0 = 1, assembled by the dense route
+ * (N <= 128; A, its kernel M and the transient take about 16 (D^2 + 2 N^4) bytes); positive
+ * semidefiniteness is then checked through the diagonal and the 2 x 2 principal minors only
+ * (a_jj >= 0, |a_jk|^2 <= a_jj a_kk).  GKSL_ERR_ARG if A is not Hermitian or fails those checks. */
 gksl_status gksl_set_kossakowski(gksl_ctx *ctx, const double *a_re, const double *a_im, double tol);
 /* Change gamma_p of an existing channel without re-expanding it. */
 gksl_status gksl_set_gamma(gksl_ctx *ctx, int p, double gamma_p);
@@ -146,6 +150,14 @@ gksl_status gksl_structure_enumerate(int N, int which, long long capacity, int *
  * environment variable GKSL_RK4_COLUMNS=32 skips them).  Both compute the same map with the same
  * arithmetic (bit-identical results). */
 #define GKSL_ASM_WIDE_COLUMNS 32u
+/* Form every dissipator channel by the dense route: R_p = Re Tr(F_s D_p(F_m)) entry by entry from
+ * the matrix-unit form of L_p rho L_p^+ - 1/2 {L_p^+ L_p, rho} (trace part of L_p included), in
+ * O(N^4) work with at most 1 GB of transient memory, N <= 200.  Without the flag a
+ * channel takes this route by itself when the sparse route's F''^T Z'' product would have more
+ * than 2 D^2 terms (a dense L at N = 100 has 5.5e9) and N <= 200, otherwise the sparse route
+ * (Sec. IV step 2.5).  Both give the same matrix up to rounding; the dense route stores R_p
+ * without its exact zeros. */
+#define GKSL_ASM_DENSE_DISSIPATORS 64u
 /* Matrix-free form: build no CSR matrix; keep H0 (+ E H1), H1, Gamma = 1/2 sum_p gamma_p L_p^+ L_p
  * and sqrt(gamma_p) L_p as complex diagonals (O(N) data) and let gksl_propagate apply Q(t) v + K on
  * the fly, as Tr(F_s L_t(rho)) with rho = 1/N + sum v F (Eq. 1, 6, 8), from tiles of rho rebuilt

@@ -92,3 +92,48 @@ def vec(X):
 
 def unvec(x, N):
     return np.asarray(x).reshape(N, N, order="F")
+
+
+def entry_vectors(N):
+    """T (scipy CSC, D x N^2) with T[j, x N + y] = (F_j)_xy for every generator j.  Column (x, y)
+    is Tr(F_j E_yx), the coefficients of the matrix unit E_yx by the basis expansion."""
+    import scipy.sparse as sp
+    cols = []
+    for x in range(N):
+        for y in range(N):
+            E = sp.csr_matrix(([1.0 + 0j], ([y], [x])), shape=(N, N))
+            cols.append(sp.csc_matrix(_b.expand_sparse(E).reshape(-1, 1)))
+    T = sp.hstack(cols).tocsc()
+    T.eliminate_zeros()
+    return T
+
+
+def kossakowski_columns(A, N, cols, T=None):
+    """Columns m in ``cols`` of R_sm = Re Tr(F_s D(F_m)) and K_s = Re Tr(F_s D(1/N)) for the Eq. 8
+    dissipator D(X) = sum_jk a_jk (F_j X F_k - 1/2 {F_k F_j, X}) of a D x D matrix A, at any N and
+    without decomposing A.  Every entry of the N x N matrices involved is a bilinear form in A of
+    the generator entries t_xy[j] = (F_j)_xy (the columns of ``entry_vectors``):
+        (sum_jk a_jk F_j E_cd F_k)_ab = t_ac^T A t_db =: P[a, c, d, b],
+        G  = sum_jk a_jk F_k F_j,   G_xy  = sum_z P[z, y, x, z],
+        G' = sum_jk a_jk F_j F_k,   G'_xy = sum_z P[x, z, z, y],
+    all of them the entries of T^T A T (two library products with the sparse T).  Then
+    D(F_m) = sum_cd (F_m)_cd P[:, c, d, :] - 1/2 (G F_m + F_m G) and D(1/N) = (G' - G)/N, each read
+    off with ``basis.expand_dense``.  Returns (R[:, cols] as a D x len(cols) array, K)."""
+    A = np.asarray(A, dtype=np.complex128)
+    if T is None:
+        T = entry_vectors(N)
+    labs = _b.labels(N)
+    AT = np.asarray(T.T @ np.ascontiguousarray(A.T)).T      # A T, D x N^2
+    P = np.asarray(T.T @ AT).reshape(N, N, N, N)             # P[a, c, d, b] = t_ac^T A t_db
+    del AT
+    G = np.einsum("zyxz->xy", P)
+    Gp = np.einsum("xzzy->xy", P)
+    R = np.zeros((len(labs), len(cols)))
+    for i, m in enumerate(cols):
+        Fm = _b.generator(N, labs[m])
+        Y = -0.5 * (G @ Fm + Fm @ G)
+        for c, d in zip(*np.nonzero(Fm)):
+            Y = Y + Fm[c, d] * P[:, c, d, :]
+        R[:, i] = _b.expand_dense(Y).real
+    K = _b.expand_dense((Gp - G) / N).real
+    return R, K

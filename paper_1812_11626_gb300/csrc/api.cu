@@ -266,6 +266,7 @@ extern "C" gksl_status gksl_set_dissipator(gksl_ctx *c, int p, double gamma, con
     return guarded(c, [&] {
         GK_REQUIRE(p >= 0 && p < GKSL_MAX_P, GKSL_ERR_ARG, "channel index out of range");
         GK_REQUIRE(std::isfinite(gamma) && gamma >= 0.0, GKSL_ERR_ARG, "gamma_p must be finite and >= 0");
+        if (c->diss[p].km) c->km_A.release();   // the Kossakowski matrix this channel held
         set_op(c, c->diss[p], rowptr, col, re, im, nnz, false);
         c->diss[p].weight = gamma;
     });
@@ -293,17 +294,18 @@ extern "C" gksl_status gksl_set_drive(gksl_ctx *c, double E, double A, double om
     });
 }
 
-// Kossakowski matrix -> channels.  A = sum_p c_p c_p^+ by a diagonally pivoted Cholesky
-// factorisation (exact for a positive semidefinite A of rank <= GKSL_MAX_P); then
-// gamma_p = |c_p|^2, l_p = c_p / |c_p|, L_p = sum_j l_pj F_j.  Any such rank factorisation gives
-// the same Lindbladian as the eigen-decomposition of Eq. 9 (the dissipator is invariant under a
-// unitary remixing of its channels).
+// Kossakowski matrix (Eq. 8).  A = sum_p c_p c_p^+ by a diagonally pivoted Cholesky factorisation
+// (exact for a positive semidefinite A of rank <= GKSL_MAX_P); then gamma_p = |c_p|^2,
+// l_p = c_p / |c_p|, L_p = sum_j l_pj F_j.  Any such rank factorisation gives the same Lindbladian
+// as the eigen-decomposition of Eq. 9 (the dissipator is invariant under a unitary remixing of its
+// channels).  A matrix of higher rank, or any A at N > 64, is kept whole on the device and
+// assembled by the dense route (dense_diss.cu) as channel 0 at unit weight.
 extern "C" gksl_status gksl_set_kossakowski(gksl_ctx *c, const double *a_re, const double *a_im, double tol) {
     return guarded(c, [&] {
         GK_REQUIRE(a_re && tol >= 0.0, GKSL_ERR_ARG, "a_re must not be null and tol >= 0");
         const long long D = c->D;
-        GK_REQUIRE(D <= 4095, GKSL_ERR_ARG, "the Kossakowski form is limited to N <= 64");
         const int N = c->N;
+        GK_REQUIRE(N <= kDenseKmMaxN, GKSL_ERR_ARG, "the Kossakowski form is limited to N <= 128");
         size_t DD = (size_t)D * D;
         std::vector<double> ar = to_host(a_re, DD, c->stream), ai = a_im ? to_host(a_im, DD, c->stream)
                                                                          : std::vector<double>(DD, 0.0);
@@ -313,53 +315,79 @@ extern "C" gksl_status gksl_set_kossakowski(gksl_ctx *c, const double *a_re, con
             mx = std::max(mx, std::hypot(ar[i], ai[i]));
         }
         for (long long j = 0; j < D; ++j)
-            for (long long k = 0; k < D; ++k)
+            for (long long k = j; k < D; ++k)
                 GK_REQUIRE(std::fabs(ar[j * D + k] - ar[k * D + j]) <= 1e-12 * mx &&
                                std::fabs(ai[j * D + k] + ai[k * D + j]) <= 1e-12 * mx,
                            GKSL_ERR_ARG, "Kossakowski matrix is not Hermitian");
-        // pivoted Cholesky on the residual R = A - sum c c^+
-        std::vector<double> rr = ar, ri = ai;
-        std::vector<std::vector<double>> cr, ci;
         double dmax0 = 0.0;
-        for (long long j = 0; j < D; ++j) dmax0 = std::max(dmax0, rr[j * D + j]);
+        for (long long j = 0; j < D; ++j) dmax0 = std::max(dmax0, ar[j * D + j]);
         const double thr = tol * std::max(dmax0, 1e-300);
-        for (;;) {
-            long long piv = -1;
-            double best = thr;
-            for (long long j = 0; j < D; ++j)
-                if (rr[j * D + j] > best) { best = rr[j * D + j]; piv = j; }
-            if (piv < 0) break;
-            GK_REQUIRE((int)cr.size() < GKSL_MAX_P, GKSL_ERR_ARG,
-                       "Kossakowski matrix has rank above the channel limit (8)");
-            double s = 1.0 / std::sqrt(best);
-            std::vector<double> vr((size_t)D), vi((size_t)D);
-            for (long long i = 0; i < D; ++i) {   // c = R[:, piv] / sqrt(R[piv, piv])
-                vr[i] = rr[i * D + piv] * s;
-                vi[i] = ri[i * D + piv] * s;
-            }
-            for (long long i = 0; i < D; ++i)
-                for (long long k = 0; k < D; ++k) {   // R -= c c^+
-                    rr[i * D + k] -= vr[i] * vr[k] + vi[i] * vi[k];
-                    ri[i * D + k] -= vi[i] * vr[k] - vr[i] * vi[k];
+        // pivoted Cholesky on the residual R = A - sum c c^+, at most GKSL_MAX_P pivots (N <= 64)
+        std::vector<std::vector<double>> cr, ci;
+        bool low_rank = false;
+        if (N <= 64) {
+            std::vector<double> rr = ar, ri = ai;
+            for (;;) {
+                long long piv = -1;
+                double best = thr;
+                for (long long j = 0; j < D; ++j)
+                    if (rr[j * D + j] > best) { best = rr[j * D + j]; piv = j; }
+                if (piv < 0) { low_rank = true; break; }
+                if ((int)cr.size() == GKSL_MAX_P) break;   // rank above the channel count: dense route
+                double sc = 1.0 / std::sqrt(best);
+                std::vector<double> vr((size_t)D), vi((size_t)D);
+                for (long long i = 0; i < D; ++i) {   // c = R[:, piv] / sqrt(R[piv, piv])
+                    vr[i] = rr[i * D + piv] * sc;
+                    vi[i] = ri[i * D + piv] * sc;
                 }
-            cr.push_back(std::move(vr));
-            ci.push_back(std::move(vi));
+                for (long long i = 0; i < D; ++i)
+                    for (long long k = 0; k < D; ++k) {   // R -= c c^+
+                        rr[i * D + k] -= vr[i] * vr[k] + vi[i] * vi[k];
+                        ri[i * D + k] -= vi[i] * vr[k] - vr[i] * vi[k];
+                    }
+                cr.push_back(std::move(vr));
+                ci.push_back(std::move(vi));
+            }
+            if (low_rank)
+                for (long long j = 0; j < D; ++j)
+                    GK_REQUIRE(rr[j * D + j] >= -std::max(thr, 1e-12 * dmax0), GKSL_ERR_ARG,
+                               "Kossakowski matrix is not positive semidefinite");
         }
-        for (long long j = 0; j < D; ++j)
-            GK_REQUIRE(rr[j * D + j] >= -std::max(thr, 1e-12 * dmax0), GKSL_ERR_ARG,
-                       "Kossakowski matrix is not positive semidefinite");
+        c->km_A.release();
+        for (int p = 0; p < GKSL_MAX_P; ++p)
+            if (c->diss[p].set) c->diss[p] = Op();
+        c->comp_dirty = true;
+        c->assembled = false;
+        if (!low_rank) {
+            // dense route: necessary conditions of positive semidefiniteness, A kept whole
+            const double eps = 1e-12 * mx;
+            double tr = 0.0;
+            for (long long j = 0; j < D; ++j) {
+                GK_REQUIRE(ar[j * D + j] >= -eps, GKSL_ERR_ARG, "Kossakowski matrix is not positive semidefinite");
+                tr += ar[j * D + j];
+            }
+            for (long long j = 0; j < D; ++j)
+                for (long long k = j + 1; k < D; ++k) {
+                    double m2 = ar[j * D + k] * ar[j * D + k] + ai[j * D + k] * ai[j * D + k];
+                    double dd = std::max(ar[j * D + j], 0.0) * std::max(ar[k * D + k], 0.0);
+                    GK_REQUIRE(m2 <= dd + eps * mx * 4.0, GKSL_ERR_ARG,
+                               "Kossakowski matrix is not positive semidefinite (a 2 x 2 principal minor is negative)");
+                }
+            std::vector<double2> h(DD);
+            for (size_t i = 0; i < DD; ++i) h[i] = make_double2(ar[i], ai[i]);
+            c->km_A.alloc(DD);
+            GK_CUDA(cudaMemcpy(c->km_A.p, h.data(), sizeof(double2) * DD, cudaMemcpyHostToDevice));
+            Op &o = c->diss[0];
+            o.set = true;
+            o.km = true;
+            o.km_trace = tr;
+            o.weight = 1.0;
+            return;
+        }
         // channels L_p = sum_j l_pj F_j as dense N x N matrices, then CSR
         Basis B(N);
         const double r2 = GK_RSQRT2;
-        for (int p = 0; p < GKSL_MAX_P; ++p) {
-            if (p >= (int)cr.size()) {
-                if (c->diss[p].set) {
-                    c->diss[p] = Op();
-                    c->comp_dirty = true;
-                    c->assembled = false;
-                }
-                continue;
-            }
+        for (int p = 0; p < (int)cr.size(); ++p) {
             double g = 0.0;
             for (long long j = 0; j < D; ++j) g += cr[p][j] * cr[p][j] + ci[p][j] * ci[p][j];
             double inv = 1.0 / std::sqrt(g);
@@ -562,6 +590,10 @@ extern "C" gksl_status gksl_min_stable_steps(gksl_ctx *c, long long *spp) {
         for (int p = 0; p < GKSL_MAX_P; ++p) {
             const Op &o = c->diss[p];
             if (!o.set) continue;
+            if (o.km) {   // sum_p gamma_p |L_p|_2^2 <= sum_p gamma_p |L_p|_F^2 = Tr A for any factorisation
+                diss += 2.0 * o.weight * o.km_trace;
+                continue;
+            }
             std::vector<double> rs((size_t)c->N, 0.0), cs((size_t)c->N, 0.0);
             for (int r = 0; r < c->N; ++r)
                 for (int e = o.h_rowptr[r]; e < o.h_rowptr[r + 1]; ++e) {

@@ -422,6 +422,15 @@ void dissipator_matrix(gksl_ctx *c, const Op &op, CsrR &R, DBuf<double> &K) {
         GK_LAUNCH_CHECK();
     }
     long long P = scan_ll(cnt.p, off.p, nnza, true, true, s);
+    if (P > 2 * D * D && c->N <= kDenseDissMaxN) {
+        // a dense operator: the product has more terms than R has entries, so form R entry by
+        // entry from the matrix-unit form instead (dense_diss.cu)
+        cnt.release();
+        off.release();
+        arow.release();
+        dense_dissipator_channel(c, op, R, K);
+        return;
+    }
     // trace-part Hamiltonian entries (complex COO, real parts used)
     Coo heff;
     if (l0.x != 0.0 || l0.y != 0.0) {
@@ -543,6 +552,8 @@ void assemble(gksl_ctx *c, unsigned flags) {
         return;
     }
     c->mf = MfBands();
+    const bool dense_diss = (flags & GKSL_ASM_DENSE_DISSIPATORS) != 0;
+    if (dense_diss != c->comp_dense) c->comp_dirty = true;
     if (c->comp_dirty) {
         for (int k = 0; k < GKSL_MAX_H0; ++k) {
             c->has_h0[k] = c->h0[k].set;
@@ -560,9 +571,12 @@ void assemble(gksl_ctx *c, unsigned flags) {
         }
         for (int p = 0; p < GKSL_MAX_P; ++p) {
             c->has_r[p] = c->diss[p].set;
-            if (c->diss[p].set) dissipator_matrix(c, c->diss[p], c->R[p], c->Kp[p]);
-            else { c->R[p] = CsrR(); c->Kp[p].release(); }
+            if (!c->diss[p].set) { c->R[p] = CsrR(); c->Kp[p].release(); }
+            else if (c->diss[p].km) dense_dissipator_kossakowski(c, c->km_A.p, c->R[p], c->Kp[p]);
+            else if (dense_diss) dense_dissipator_channel(c, c->diss[p], c->R[p], c->Kp[p]);
+            else dissipator_matrix(c, c->diss[p], c->R[p], c->Kp[p]);
         }
+        c->comp_dense = dense_diss;
         c->comp_dirty = false;
     }
     // K = sum_p gamma_p K_p

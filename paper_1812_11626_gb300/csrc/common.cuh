@@ -189,6 +189,8 @@ struct Op {
     std::vector<int> h_rowptr, h_col;      // host copies (validation, stability bound)
     std::vector<double> h_re, h_im;
     double weight = 0.0;   // theta_k or gamma_p
+    bool km = false;       // dissipator channel holding a whole Kossakowski matrix (gksl_ctx::km_A)
+    double km_trace = 0.0; // Tr A of that matrix (the stability bound's dissipator norm)
 };
 
 }  // namespace gk
@@ -218,6 +220,8 @@ struct gksl_ctx {
     gk::DBuf<double> Kp[GKSL_MAX_P];
     bool has_h0[GKSL_MAX_H0] = {};
     bool has_r[GKSL_MAX_P] = {};
+    gk::DBuf<double2> km_A;    // Kossakowski matrix of the dense route (D x D), see Op::km
+    bool comp_dense = false;   // components built with GKSL_ASM_DENSE_DISSIPATORS
 
     // combined, rebuilt when a weight or E changes
     bool assembled = false;

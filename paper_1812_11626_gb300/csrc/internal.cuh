@@ -53,6 +53,14 @@ void mf_post(gksl_ctx *c, int precision);
 // the four stages of one RK4 step
 void mf_step(gksl_ctx *c, int precision, double h, const double *tab, long long local);
 
+// ---- dense_diss.cu (dissipators through their matrix-unit form, O(N^4); Eq. 8)
+constexpr int kDenseDissMaxN = 200;   // dense R: D^2 < 2^31 entries
+constexpr int kDenseKmMaxN = 128;     // Kossakowski kernel M: N^4 complex (4.3 GB at N = 128)
+// R (unit rate, CSR without exact zeros) and K of one jump operator, any N x N matrix
+void dense_dissipator_channel(gksl_ctx *c, const Op &op, CsrR &R, DBuf<double> &K);
+// R and K of the Eq. 8 dissipator of a D x D Kossakowski matrix (device, row-major)
+void dense_dissipator_kossakowski(gksl_ctx *c, const double2 *A, CsrR &R, DBuf<double> &K);
+
 // ---- adjoint.cu
 void adjoint_timeavg(gksl_ctx *c, const double *o_diag_dev, long long spp, long long period, int precision,
                      double *loss, double *grad, int n_grad);

@@ -818,6 +818,8 @@ void mf_build(gksl_ctx *c, bool fp32) {
     std::vector<int> chans;
     for (int p = 0; p < GKSL_MAX_P; ++p)
         if (c->diss[p].set) {
+            GK_REQUIRE(!c->diss[p].km, GKSL_ERR_ARG,
+                       "the matrix-free form needs jump operators, not a full-rank Kossakowski matrix");
             chans.push_back(p);
             bl = std::max(bl, half_bandwidth(c->diss[p]));
             real = real && op_real(c->diss[p]);

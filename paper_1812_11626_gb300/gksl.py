@@ -22,6 +22,7 @@ GKSL_MAX_P = 8
 GKSL_STRUCT_F, GKSL_STRUCT_D = 0, 1
 GKSL_ASM_FP32, GKSL_ASM_TRANSPOSE, GKSL_ASM_NO_DROP, GKSL_ASM_MATRIX_FREE, GKSL_ASM_NO_FOLD = 1, 2, 4, 8, 16
 GKSL_ASM_WIDE_COLUMNS = 32
+GKSL_ASM_DENSE_DISSIPATORS = 64
 GKSL_MAT_Q0, GKSL_MAT_Q1, GKSL_MAT_H0, GKSL_MAT_R = 0, 1, 16, 32
 
 if not os.path.exists(LIB_PATH):

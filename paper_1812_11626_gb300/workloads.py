@@ -198,3 +198,21 @@ def random_density_matrix(N, rank, seed):
     rho /= np.trace(rho).real
     rho = 0.5 * (rho + rho.conj().T)
     return np.ascontiguousarray(rho.real), np.ascontiguousarray(rho.imag)
+
+
+def random_kossakowski(N, seed, scale=1.0):
+    """Seeded full-rank Kossakowski matrix over the N^2 - 1 generators: A = c 1 + H with H a
+    Hermitian Gaussian matrix (entries of variance scale^2 / D) and c = 3 scale, three times the
+    radius of H's spectrum (about 2 scale), so A is positive definite.  Returns (re, im).  H is
+    symmetrised tile by tile (a whole-matrix transpose of D^2 entries is slow)."""
+    D = N * N - 1
+    rng = np.random.default_rng(seed)
+    X = (rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))) * (scale / np.sqrt(2 * D))
+    H = np.empty((D, D), dtype=np.complex128)
+    tb = 512
+    for i0 in range(0, D, tb):
+        for j0 in range(0, D, tb):
+            H[i0:i0 + tb, j0:j0 + tb] = (X[i0:i0 + tb, j0:j0 + tb] + X[j0:j0 + tb, i0:i0 + tb].conj().T) / np.sqrt(2.0)
+    del X
+    H[np.diag_indices(D)] += 3.0 * scale
+    return np.ascontiguousarray(H.real), np.ascontiguousarray(H.imag)

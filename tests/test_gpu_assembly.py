@@ -180,8 +180,9 @@ def test_assembly_dimer_n1000_full(G, record):
 
 
 def test_kossakowski_matrix_vs_eq8(G):
-    """General dissipator from a rank-3 Kossakowski matrix (Eq. 8) against the oracle's Eq. 8 applied
-    with A directly; a rank-9 matrix and an indefinite one are rejected."""
+    """General dissipator from a rank-3 Kossakowski matrix (Eq. 8, factorised into three channels)
+    against the oracle's Eq. 8 applied with A directly; a rank-9 matrix (more channels than
+    GKSL_MAX_P) takes the dense route and matches too; an indefinite one is rejected."""
     N = 5
     M = N * N - 1
     rng = np.random.default_rng(21)
@@ -199,10 +200,16 @@ def test_kossakowski_matrix_vs_eq8(G):
         K = np.zeros(M)
         G.gksl_get_k(ctx, K)
         assert np.abs(K - Kr).max() < TOL_ASM * np.abs(Qr).max()
+        assert G.gksl_get_info(ctx).nnz_r[2] > 0   # three channels
         C9 = rng.normal(size=(M, 9)) + 1j * rng.normal(size=(M, 9))
-        A9 = C9 @ C9.conj().T
-        with pytest.raises(G.GkslError):
-            G.gksl_set_kossakowski(ctx, A9.real.copy(), A9.imag.copy())
+        A9 = C9 @ C9.conj().T * 0.05
+        G.gksl_set_kossakowski(ctx, A9.real.copy(), A9.imag.copy())
+        G.gksl_assemble(ctx, 0)
+        assert G.gksl_get_info(ctx).nnz_r[1] == 0   # one channel holds the whole matrix
+        Qr, Kr = OL.unfold_dense_kossakowski(H.to_dense(), A9)
+        assert rel_err(csr_of(G, ctx, G.GKSL_MAT_Q0).toarray(), Qr) < TOL_ASM
+        G.gksl_get_k(ctx, K)
+        assert np.abs(K - Kr).max() < TOL_ASM * np.abs(Qr).max()
         Aneg = A.copy()
         Aneg[0, 0] -= 10 * np.abs(A).max()
         with pytest.raises(G.GkslError):

@@ -536,3 +536,17 @@ def test_loss_of_a_constant_observable_is_the_constant():
         L = P.timeavg_loss(Q0, u.Q1, d.rate * u.K1, P.eps_fn(p["E"], p["A"], p["omega"]), SYS.initial_v(d), w, c0,
                            2 * np.pi / S, S, period)
         assert abs(L - 2.5) < 1e-13
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_kossakowski_columns_match_eq8_applied_directly(N):
+    """The column-wise Eq. 8 oracle (bilinear forms of generator entries, any N) against Eq. 8
+    applied with dense generator matrices (lindbladian_kossakowski), full-rank A, every column."""
+    re, im = W.random_kossakowski(N, 40 + N)
+    A = re + 1j * im
+    assert np.linalg.eigvalsh(A).min() > 0
+    D = N * N - 1
+    Q, K = Lb.unfold_dense_kossakowski(np.zeros((N, N), complex), A)
+    R, K2 = Lb.kossakowski_columns(A, N, list(range(D)))
+    assert np.abs(R - Q).max() < 1e-14 * np.abs(Q).max()
+    assert np.abs(K - K2).max() < 1e-14 * np.abs(Q).max()
