@@ -254,6 +254,19 @@ gksl_status gksl_batch_reset(gksl_batch *b);
  * whole run. */
 gksl_status gksl_batch_propagate(gksl_batch *b, const long long *steps_per_period, const long long *n_steps,
                                  long long correction_every, double *seconds);
+/* Long-time (Floquet) asymptotic state of every instance (Sec. I: the asymptotic state is
+ * T-periodic; Sec. V: populations read at phase 0 after a transient of 10 T).  Propagates
+ * `transient` whole periods, then period by period until every instance's period-map residual
+ *     r_b = max_s |v_b(kT) - v_b((k-1)T)|
+ * is <= tol, or max_periods periods after the transient.  Group g advances steps_per_period[g]
+ * steps per period with the arithmetic of gksl_batch_propagate (FP32 bulk, one FP64 step every
+ * correction_every steps; 1: FP64 throughout).  residual (n_instances doubles, batch instance
+ * order, host memory) receives each instance's last r_b (+inf where the state went non-finite);
+ * periods (may be NULL) the total periods run, transient included.  Returns GKSL_OK whether or
+ * not tol was met; the states are left at the last period end. */
+gksl_status gksl_batch_asymptotic(gksl_batch *b, const long long *steps_per_period, long long transient,
+                                  long long max_periods, double tol, long long correction_every, double *residual,
+                                  long long *periods);
 /* State of instance i (D_i doubles, FP64 master). */
 gksl_status gksl_batch_get_state(gksl_batch *b, int instance, double *v);
 /* Tile width chosen by the autotuner for group `group` (instances per lane; one warp covers

@@ -128,3 +128,15 @@ def expand_dense(X):
     below = np.cumsum(d)[:-1]                      # sum_{k<l} X_kk for l = 1..N-1
     dpart = (below - l * d[1:]) / np.sqrt(l * (l + 1.0))
     return np.concatenate([(up + lo) / np.sqrt(2.0), 1j * (up - lo) / np.sqrt(2.0), dpart])
+
+
+def populations_from_v(v, N):
+    """diag rho of Eq. 6: rho_jj = 1/N + sum_l v_{D^l} (D^l)_jj, with (D^l)_jj = c_l for j < l,
+    -l c_l for j = l and 0 above (only the D generators have diagonal entries)."""
+    vd = np.asarray(v, dtype=float)[2 * n_pairs(N):]
+    pop = np.full(N, 1.0 / N)
+    for l in range(1, N):
+        c = 1.0 / np.sqrt(l * (l + 1.0))
+        pop[:l] += vd[l - 1] * c
+        pop[l] -= vd[l - 1] * l * c
+    return pop

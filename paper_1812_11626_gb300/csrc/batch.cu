@@ -16,6 +16,7 @@
 // in CUDA graphs.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -305,6 +306,8 @@ struct Group {
     double h = 0.0;
     double t = 0.0;   // time of the group's states
     double tuned_us = 0.0;
+    DBuf<double> Vprev;                 // state one period earlier (gksl_batch_asymptotic)
+    DBuf<unsigned long long> resid;     // per-instance period-map residual, as double bit patterns
 };
 
 }  // namespace
@@ -694,65 +697,146 @@ extern "C" gksl_status gksl_batch_reset(gksl_batch *b) {
     return bguarded(b, [&] { reset_batch(b); });
 }
 
+namespace gk {
+namespace {
+
+// n_steps[g] RK4 steps of every group g at h = T / steps_per_period[g] (FP32 bulk, an FP64 step
+// every correction_every steps); returns the device time in milliseconds
+double batch_advance(gksl_batch *b, const long long *spp, const long long *n_steps, long long correction_every) {
+    GK_REQUIRE(spp && n_steps, GKSL_ERR_ARG, "steps_per_period and n_steps arrays required");
+    if (!b->tuned) autotune(b);
+    long long maxsteps = 0;
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+        Group &G = b->groups[i];
+        GK_REQUIRE(spp[i] > 0 && n_steps[i] >= 0, GKSL_ERR_ARG, "steps_per_period > 0 and n_steps >= 0 required");
+        double T = 2.0 * M_PI / G.ctx->omega;
+        double h = T / (double)spp[i];
+        long long n = n_steps[i];
+        if (G.ctx->drive_shape == GKSL_DRIVE_SQUARE) {
+            double k = G.t / h;
+            GK_REQUIRE(spp[i] % 2 == 0 && std::fabs(k - std::nearbyint(k)) <= 1e-6 * std::max(1.0, std::fabs(k)),
+                       GKSL_ERR_ARG, "the square drive needs an even steps_per_period and times on the step grid");
+        }
+        if (G.h != h || G.nsteps != n) clear_batch_graphs(b);
+        G.h = h;
+        G.nsteps = n;
+        if (G.sin_tab.n < (size_t)(3 * std::max(1LL, n))) {
+            G.sin_tab.alloc((size_t)(3 * std::max(1LL, n)));
+            G.sin_tab_f.alloc((size_t)(3 * std::max(1LL, n)));
+            clear_batch_graphs(b);
+        }
+        if (n > 0) {
+            k_sin_table<<<grid_for(n, 256), 256, 0, b->stream>>>(G.t, h, G.ctx->omega, G.ctx->drive_shape, n,
+                                                                 G.sin_tab.p, G.sin_tab_f.p);
+            GK_LAUNCH_CHECK();
+        }
+        G.t += (double)n * h;
+        maxsteps = std::max(maxsteps, n);
+    }
+    cudaEvent_t e0, e1;
+    GK_CUDA(cudaEventCreate(&e0));
+    GK_CUDA(cudaEventCreate(&e1));
+    GK_CUDA(cudaEventRecord(e0, b->stream));
+    long long n = 0;
+    while (n < maxsteps) {
+        long long stop = maxsteps;
+        long long corr = -1;
+        if (correction_every > 0) corr = (n / correction_every + 1) * correction_every - 1;
+        if (corr >= 0 && corr < stop) {
+            if (corr > n) run_batch_steps(b, false, n, corr - n);
+            run_batch_steps(b, true, corr, 1);
+            n = corr + 1;
+        } else {
+            run_batch_steps(b, false, n, stop - n);
+            n = stop;
+        }
+    }
+    GK_CUDA(cudaEventRecord(e1, b->stream));
+    GK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (double)ms;
+}
+
+// r_b = max_{r < D} |V[r, b] - P[r, b]| for every instance b, as the bit pattern of a non-negative
+// double (the unsigned order of those patterns is the order of the values); a non-finite
+// difference counts as +inf.  Block (32, 8): 32 consecutive instances, rows strided over y.
+__global__ void k_period_residual(const double *__restrict__ V, const double *__restrict__ P, long long D,
+                                  long long Bs, int B, unsigned long long *__restrict__ out) {
+    const int b = blockIdx.x * 32 + threadIdx.x;
+    if (b >= B) return;
+    double m = 0.0;
+    for (long long r = (long long)blockIdx.y * blockDim.y + threadIdx.y; r < D; r += (long long)gridDim.y * blockDim.y) {
+        double d = fabs(V[r * Bs + b] - P[r * Bs + b]);
+        if (d != d) d = INFINITY;
+        m = d > m ? d : m;
+    }
+    if (m > 0.0) atomicMax(out + b, (unsigned long long)__double_as_longlong(m));
+}
+
+}  // namespace
+}  // namespace gk
+
 extern "C" gksl_status gksl_batch_propagate(gksl_batch *b, const long long *spp, const long long *n_steps,
                                             long long correction_every, double *seconds) {
     return bguarded(b, [&] {
         NvtxRange r("gksl_batch_propagate");
-        GK_REQUIRE(spp && n_steps, GKSL_ERR_ARG, "steps_per_period and n_steps arrays required");
-        if (!b->tuned) autotune(b);
-        long long maxsteps = 0;
-        for (size_t i = 0; i < b->groups.size(); ++i) {
-            Group &G = b->groups[i];
-            GK_REQUIRE(spp[i] > 0 && n_steps[i] >= 0, GKSL_ERR_ARG, "steps_per_period > 0 and n_steps >= 0 required");
-            double T = 2.0 * M_PI / G.ctx->omega;
-            double h = T / (double)spp[i];
-            long long n = n_steps[i];
-            if (G.ctx->drive_shape == GKSL_DRIVE_SQUARE) {
-                double k = G.t / h;
-                GK_REQUIRE(spp[i] % 2 == 0 && std::fabs(k - std::nearbyint(k)) <= 1e-6 * std::max(1.0, std::fabs(k)),
-                           GKSL_ERR_ARG, "the square drive needs an even steps_per_period and times on the step grid");
-            }
-            if (G.h != h || G.nsteps != n) clear_batch_graphs(b);
-            G.h = h;
-            G.nsteps = n;
-            if (G.sin_tab.n < (size_t)(3 * std::max(1LL, n))) {
-                G.sin_tab.alloc((size_t)(3 * std::max(1LL, n)));
-                G.sin_tab_f.alloc((size_t)(3 * std::max(1LL, n)));
-                clear_batch_graphs(b);
-            }
-            if (n > 0) {
-                k_sin_table<<<grid_for(n, 256), 256, 0, b->stream>>>(G.t, h, G.ctx->omega, G.ctx->drive_shape, n,
-                                                                     G.sin_tab.p, G.sin_tab_f.p);
-                GK_LAUNCH_CHECK();
-            }
-            G.t += (double)n * h;
-            maxsteps = std::max(maxsteps, n);
-        }
-        cudaEvent_t e0, e1;
-        GK_CUDA(cudaEventCreate(&e0));
-        GK_CUDA(cudaEventCreate(&e1));
-        GK_CUDA(cudaEventRecord(e0, b->stream));
-        long long n = 0;
-        while (n < maxsteps) {
-            long long stop = maxsteps;
-            long long corr = -1;
-            if (correction_every > 0) corr = (n / correction_every + 1) * correction_every - 1;
-            if (corr >= 0 && corr < stop) {
-                if (corr > n) run_batch_steps(b, false, n, corr - n);
-                run_batch_steps(b, true, corr, 1);
-                n = corr + 1;
-            } else {
-                run_batch_steps(b, false, n, stop - n);
-                n = stop;
-            }
-        }
-        GK_CUDA(cudaEventRecord(e1, b->stream));
-        GK_CUDA(cudaEventSynchronize(e1));
-        float ms = 0;
-        GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        double ms = batch_advance(b, spp, n_steps, correction_every);
         if (seconds) *seconds = ms * 1e-3;
+    });
+}
+
+extern "C" gksl_status gksl_batch_asymptotic(gksl_batch *b, const long long *spp, long long transient,
+                                             long long max_periods, double tol, long long correction_every,
+                                             double *residual, long long *periods) {
+    return bguarded(b, [&] {
+        NvtxRange r("gksl_batch_asymptotic");
+        GK_REQUIRE(spp && residual && transient >= 0 && max_periods >= 1 && tol >= 0.0, GKSL_ERR_ARG,
+                   "steps_per_period and residual required, transient >= 0, max_periods >= 1, tol >= 0");
+        const size_t ng = b->groups.size();
+        std::vector<long long> per(spp, spp + ng), none(ng, 0);
+        for (size_t g = 0; g < ng; ++g) GK_REQUIRE(per[g] > 0, GKSL_ERR_ARG, "steps_per_period > 0 required");
+        if (transient > 0) {
+            std::vector<long long> n(ng);
+            for (size_t g = 0; g < ng; ++g) n[g] = per[g] * transient;
+            batch_advance(b, per.data(), n.data(), correction_every);
+        }
+        std::vector<double> res((size_t)b->n_instances, 0.0);
+        long long k = 0;
+        for (;;) {
+            for (auto &G : b->groups) {
+                const size_t n = (size_t)((G.D + 1) * G.Bs);
+                if (G.Vprev.n < n) G.Vprev.alloc(n);
+                if (G.resid.n < (size_t)G.B) G.resid.alloc((size_t)G.B);
+                GK_CUDA(cudaMemcpyAsync(G.Vprev.p, G.V64.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+                GK_CUDA(cudaMemsetAsync(G.resid.p, 0, sizeof(unsigned long long) * G.B, b->stream));
+            }
+            batch_advance(b, per.data(), per.data(), correction_every);
+            ++k;
+            double worst = 0.0;
+            for (size_t g = 0; g < ng; ++g) {
+                Group &G = b->groups[g];
+                const long long ry = std::min<long long>((G.D + 7) / 8, 1024);
+                k_period_residual<<<dim3((unsigned)((G.B + 31) / 32), (unsigned)ry), dim3(32, 8), 0, b->stream>>>(
+                    G.V64.p, G.Vprev.p, G.D, G.Bs, G.B, G.resid.p);
+                GK_LAUNCH_CHECK();
+                std::vector<unsigned long long> bits((size_t)G.B);
+                GK_CUDA(cudaMemcpyAsync(bits.data(), G.resid.p, sizeof(unsigned long long) * G.B,
+                                        cudaMemcpyDeviceToHost, b->stream));
+                GK_CUDA(cudaStreamSynchronize(b->stream));
+                for (int i = 0; i < G.B; ++i) {
+                    double x;
+                    std::memcpy(&x, &bits[(size_t)i], sizeof(double));
+                    res[(size_t)(b->first_instance[g] + i)] = x;
+                    worst = std::max(worst, x);
+                }
+            }
+            if (worst <= tol || k >= max_periods) break;
+        }
+        std::memcpy(residual, res.data(), sizeof(double) * res.size());
+        if (periods) *periods = transient + k;
     });
 }
 

@@ -91,6 +91,7 @@ _SIGS = {
     "gksl_batch_get_state": (_S, [_P, _I, _P]),
     "gksl_batch_info": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "gksl_batch_set_scan": (_S, [_P, _I, _P]),
+    "gksl_batch_asymptotic": (_S, [_P, _P, _L, _L, _D, _L, _P, ctypes.POINTER(_L)]),
     "gksl_get_info": (_S, [_P, ctypes.POINTER(gksl_info)]),
     "gksl_propagate_csr_noalloc": (_S, [_L, _P, _P, _P, _P, _P, _P, _P, _P, _D, _D, _L, _D, _D, _D, _P]),
 }
@@ -309,6 +310,16 @@ def gksl_batch_set_scan(b, component, theta_b):
     _check(_lib.gksl_batch_set_scan(b, int(component), _ptr(th)), batch=b)
 
 
+def gksl_batch_asymptotic(b, steps_per_period, transient, max_periods, tol, correction_every, n_instances):
+    """Returns (residual per instance, total periods run)."""
+    spp = np.ascontiguousarray(steps_per_period, dtype=np.int64)
+    res = np.zeros(int(n_instances))
+    per = _L()
+    _check(_lib.gksl_batch_asymptotic(b, _ptr(spp), int(transient), int(max_periods), float(tol),
+                                      int(correction_every), _ptr(res), ctypes.byref(per)), batch=b)
+    return res, per.value
+
+
 def gksl_batch_info(b, group):
     ipl, us = _I(), _D()
     _check(_lib.gksl_batch_info(b, int(group), ctypes.byref(ipl), ctypes.byref(us)), batch=b)
@@ -453,10 +464,15 @@ def dimer_batch(instances, device=0):
     return gksl_batch_create(ctxs, n_inst, A, g), ctxs, groups
 
 
-def bifurcation_scan(N, U_values, periods, steps_per_period=None, device=0, params=None):
-    """Populations diag rho(t = periods * T) of the driven dimer for every interaction U in U_values,
-    propagated together as one batch (the quantum bifurcation diagram of Sec. III / Sec. V at
-    t_s = 0 after a transient of `periods` periods).  Returns (populations [len(U), N], spp)."""
+def bifurcation_scan(N, U_values, transient=10, tol=0.0, max_periods=1, steps_per_period=None, device=0,
+                     params=None, correction_every=None):
+    """Populations diag rho at phase 0 of the driven dimer's long-time state for every interaction U
+    in U_values, propagated together as one batch (the quantum bifurcation diagram of Sec. III /
+    Sec. V): `transient` periods, then period by period until every instance's period-map residual
+    max_s |v(kT) - v((k-1)T)| is <= tol or `max_periods` more periods have run
+    (gksl_batch_asymptotic).  FP32 bulk with one FP64 step per period unless `correction_every`
+    says otherwise (1: FP64 throughout).
+    Returns (populations [len(U), N], steps per period, residual per U, total periods run)."""
     from . import workloads as W
     d = W.dimer(N, params)
     ctx = dimer_context(d, device=device, flags=GKSL_ASM_FP32)
@@ -470,9 +486,12 @@ def bifurcation_scan(N, U_values, periods, steps_per_period=None, device=0, para
             steps_per_period += steps_per_period % 2
             gksl_set_theta(ctx, 1, p["U"])
             gksl_assemble(ctx, GKSL_ASM_FP32)
+        if correction_every is None:
+            correction_every = steps_per_period
         b = gksl_batch_create([ctx], [n], [p["A"]] * n, [1.0] * n)
         gksl_batch_set_scan(b, 1, U_values)
-        gksl_batch_propagate(b, [steps_per_period], [steps_per_period * periods], steps_per_period)
+        residual, periods = gksl_batch_asymptotic(b, [steps_per_period], transient, max_periods, tol,
+                                                  correction_every, n)
         D = N * N - 1
         pops = np.zeros((n, N))
         v = np.zeros(D)
@@ -481,7 +500,7 @@ def bifurcation_scan(N, U_values, periods, steps_per_period=None, device=0, para
             gksl_batch_get_state(b, i, v)
             gksl_rho(ctx, v, re, im)
             pops[i] = np.diag(re)
-        return pops, steps_per_period
+        return pops, steps_per_period, residual, periods
     finally:
         if b is not None:
             gksl_batch_destroy(b)

@@ -85,7 +85,8 @@ def test_bifurcation_scan_vs_oracle(G):
     populations are a probability distribution."""
     N = 12
     U = np.linspace(0.0, 1.4, 8)
-    pops, spp = G.bifurcation_scan(N, U, periods=2)
+    pops, spp, res, per = G.bifurcation_scan(N, U, transient=1, max_periods=1)
+    assert per == 2 and np.all(np.isfinite(res)) and res.max() > 0
     from oracle import basis as OB
     for i in (0, 3, 7):
         d = W.dimer(N, dict(U=float(U[i])))
@@ -113,3 +114,54 @@ def test_batch_fp64_correction_only_matches_fp64(G):
             G.gksl_batch_destroy(b)
     finally:
         G.gksl_destroy(ctx)
+
+
+def test_asymptotic_state_converges_vs_oracle(G, record):
+    """Floquet asymptotic state (Sec. I, Sec. V): N = 20, eight interactions U, FP64 throughout;
+    after the transient of 10 periods the batch runs period by period until every instance's
+    period-map residual max |v(kT) - v((k-1)T)| <= 1e-8.  The residuals and the populations at the
+    final period end match the oracle's RK4 run for the same number of periods (its residual taken
+    from its own period-end states)."""
+    from oracle import basis as OB
+    from oracle import propagate as OP
+    N = 20
+    U = np.linspace(0.1, 1.0, 8)
+    pops, spp, res, per = G.bifurcation_scan(N, U, transient=10, tol=1e-8, max_periods=80, correction_every=1)
+    record("periods_to_1e-8", per)
+    assert np.all(res <= 1e-8) and 10 < per < 90, (per, res.max())
+    for i in (0, 4, 7):
+        d = W.dimer(N, dict(U=float(U[i])))
+        u = SYS.unfold_dimer(d)
+        _, outs = SYS.propagate_dimer(d, u, spp, per * spp, emit_every=spp, threaded=True)
+        r_ref = np.abs(outs[-1] - outs[-2]).max()
+        ref = np.real(np.diag(OB.rho_from_v(outs[-1], N=N)))
+        assert np.abs(pops[i] - ref).max() < 1e-10, (i, np.abs(pops[i] - ref).max())
+        assert abs(res[i] - r_ref) <= 1e-12 + 1e-6 * r_ref, (i, res[i], r_ref)
+
+
+def test_bifurcation_scan_n100_32_values_vs_oracle(G, record):
+    """The bifurcation diagram at size: N = 100 (D = 9 999), 32 interactions U in [0.05, 1], one
+    batch, FP32 bulk with an FP64 step per period, the paper's transient of 10 periods and one
+    more period for the residual; populations and the state of three sampled U values against the
+    oracle's FP64 RK4 (FP32 tolerances: 1e-5 on v, 1e-4 on populations)."""
+    import time
+    from oracle import basis as OB
+    N = 100
+    U = np.linspace(0.05, 1.0, 32)
+    t0 = time.perf_counter()
+    pops, spp, res, per = G.bifurcation_scan(N, U, transient=10, max_periods=1)
+    sec = time.perf_counter() - t0
+    record("steps_per_period", spp)
+    record("instance_steps_per_s_incl_assembly", 32 * per * spp / sec)
+    record("max_period_residual", res.max())
+    assert per == 11 and np.all(np.isfinite(res))
+    assert np.abs(pops.sum(1) - 1).max() < 1e-10 and pops.min() > -1e-6
+    worst = 0.0
+    for i in (0, 15, 31):
+        d = W.dimer(N, dict(U=float(U[i])))
+        u = SYS.unfold_dimer(d)
+        v_ref, _ = SYS.propagate_dimer(d, u, spp, per * spp, threaded=True)
+        ref = OB.populations_from_v(v_ref, N)
+        worst = max(worst, np.abs(pops[i] - ref).max())
+        assert np.abs(pops[i] - ref).max() < 1e-4, (i, np.abs(pops[i] - ref).max())
+    record("max_abs_population_diff_vs_oracle", worst)

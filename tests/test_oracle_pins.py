@@ -550,3 +550,14 @@ def test_kossakowski_columns_match_eq8_applied_directly(N):
     R, K2 = Lb.kossakowski_columns(A, N, list(range(D)))
     assert np.abs(R - Q).max() < 1e-14 * np.abs(Q).max()
     assert np.abs(K - K2).max() < 1e-14 * np.abs(Q).max()
+
+
+def test_populations_from_v_match_rho():
+    """diag of the Eq. 6 reconstruction with the dense basis equals the D-generator formula."""
+    for N in (2, 3, 6):
+        rng = np.random.default_rng(N)
+        X = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+        rho = X @ X.conj().T
+        rho /= np.trace(rho)
+        v = B.expand(rho).real
+        assert np.abs(B.populations_from_v(v, N) - np.diag(rho).real).max() < 1e-15
