@@ -303,6 +303,17 @@ gksl_status gksl_propagate_csr_noalloc(long long D, const int *a0_rowptr, const 
                                        const double *K, double *v, double t0, double h, long long n_steps, double E,
                                        double A, double omega, void *cuda_stream);
 
+/* ------------------------------------------------------------------ measured rates */
+
+/* The paper has no counterpart to this call; it measures two rates of GPU `device` that bound
+ * this library's kernels and for which no vendor figure applies as measured: the FP64 fused
+ * multiply-add rate (FMA per second, each counted once) of a grid of independent FMA chains, and
+ * the rate of reading an L2-resident 32 MiB buffer (bytes per second).  Either pointer may be
+ * NULL (not measured).  Each probe checks its own result (the FMA chains against the same
+ * recurrence on the host, the L2 sum against its exact value) and returns GKSL_ERR_STATE if it
+ * fails; GKSL_ERR_CUDA on a CUDA error.  Takes about 0.2 s; restores the calling thread's device. */
+gksl_status gksl_measure_rates(int device, double *fp64_fma_per_s, double *l2_read_bytes_per_s);
+
 /* ------------------------------------------------------------------ introspection */
 
 typedef struct {

@@ -93,6 +93,7 @@ _SIGS = {
     "gksl_batch_set_scan": (_S, [_P, _I, _P]),
     "gksl_batch_asymptotic": (_S, [_P, _P, _L, _L, _D, _L, _P, ctypes.POINTER(_L)]),
     "gksl_get_info": (_S, [_P, ctypes.POINTER(gksl_info)]),
+    "gksl_measure_rates": (_S, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "gksl_propagate_csr_noalloc": (_S, [_L, _P, _P, _P, _P, _P, _P, _P, _P, _D, _D, _L, _D, _D, _D, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -330,6 +331,15 @@ def gksl_get_info(ctx):
     info = gksl_info()
     _check(_lib.gksl_get_info(ctx, ctypes.byref(info)), ctx)
     return info
+
+
+def gksl_measure_rates(device=0):
+    """(FP64 FMA per second, L2-resident read bytes per second) of the GPU, both self-checked."""
+    f, l2 = _D(), _D()
+    st = _lib.gksl_measure_rates(int(device), ctypes.byref(f), ctypes.byref(l2))
+    if st != GKSL_OK:
+        raise GkslError(st, "gksl_measure_rates: a rate probe failed its own check or a CUDA call failed")
+    return f.value, l2.value
 
 
 GKSL_NOALLOC_MAX_D = 262144

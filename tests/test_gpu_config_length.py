@@ -65,7 +65,7 @@ def test_batch_256_one_full_period_per_group_vs_oracle(G, record):
     b, ctxs, groups = G.dimer_batch(inst)
     try:
         spps = [spp for _, _, spp in groups]
-        G.gksl_batch_propagate(b, spps, spps, spps)
+        G.gksl_batch_propagate(b, spps, spps, min(spps))   # an FP64 step every min(spp) steps
         pos, worst_v, worst_o = 0, 0.0, 0.0
         for N, idx, spp in groups:
             for j in (0, len(idx) // 2, len(idx) - 1):
