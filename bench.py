@@ -167,7 +167,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import scipy.sparse  # noqa: F401
-    from oracle import native, propagate as OP, system as SYS
+    from oracle import native, system as SYS
     from paper_1812_11626_gb300 import workloads as W
     native.build()
     d = W.dimer(N_BENCH)
@@ -179,14 +179,18 @@ def run_reference(args, rank, world):
     K = d.rate * u.K1
     spp = stable_spp_estimate(d)
     h = 2 * np.pi / p["omega"] / spp
-    eps = OP.eps_fn(p["E"], p["A"], p["omega"])
     v = SYS.initial_v(d)
-    sample = 8   # RK4 steps per bench step of the reference arm (bounded sample)
+    sysc = native.Rk4System(Q0, u.Q1, K, len(v))
+    threads = native.rk4_threads()
+    sample = 32   # RK4 steps per bench step of the reference arm (bounded sample)
+    n = 0
     for _ in range(args.warmup):
-        v, _ = OP.rk4(Q0, u.Q1, K, eps, v, h, sample)
+        v, _ = sysc.run(p["E"], p["A"], p["omega"], v, h, sample, t0=n * h)
+        n += sample
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, _ = OP.rk4(Q0, u.Q1, K, eps, v, h, sample)
+        v, _ = sysc.run(p["E"], p["A"], p["omega"], v, h, sample, t0=n * h)
+        n += sample
     el = time.perf_counter() - t0
     val = args.steps * sample / el
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
@@ -194,9 +198,9 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "driven Bose dimer N=1000 (D=999999), FP64 RK4 at the stable step", "N": N_BENCH,
                        "rk4_steps_per_bench_step": sample, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{sample} RK4 steps per bench step (scipy CSR SpMV, single thread); "
-                                       f"oracle assembly {asm_s:.1f} s untimed"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} RK4 steps per bench step (the oracle's C RK4 on {threads} OpenMP "
+                                       f"threads); oracle assembly {asm_s:.1f} s untimed"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "oracle_assembly_s": asm_s}
     print(json.dumps(line), flush=True)
@@ -220,7 +224,9 @@ def stable_spp_estimate(d):
 # ---------------------------------------------------------------------- GPU arm
 
 def cpu_baseline_sample():
-    """The oracle as it stands on this host: assembly, then a bounded number of RK4 steps."""
+    """The oracle as it stands on this host: its assembly, then bounded samples of RK4 steps with
+    the threaded C RK4 on every host core (about 10 s) and, for context, with scipy's CSR product
+    on one thread (about 5 s)."""
     from oracle import native, propagate as OP, system as SYS
     from paper_1812_11626_gb300 import workloads as W
     native.build()
@@ -230,20 +236,33 @@ def cpu_baseline_sample():
     asm_s = time.perf_counter() - t0
     p = d.params
     Q0 = u.q0(p["J"], p["U"], d.rate)
+    K = d.rate * u.K1
     spp = stable_spp_estimate(d)
     h = 2 * np.pi / p["omega"] / spp
     v = SYS.initial_v(d)
-    # a bounded sample of about 10 s of CPU work: RK4 steps until 10 s have passed (at least 16)
+    sysc = native.Rk4System(Q0, u.Q1, K, len(v))
+    threads = native.rk4_threads()
     n, el = 0, 0.0
-    eps = OP.eps_fn(p["E"], p["A"], p["omega"])
     t0 = time.perf_counter()
     while n < 16 or el < 10.0:
-        v, _ = OP.rk4(Q0, u.Q1, d.rate * u.K1, eps, v, h, 8, t0=n * h)
+        v, _ = sysc.run(p["E"], p["A"], p["omega"], v, h, 8, t0=n * h)
         n += 8
         el = time.perf_counter() - t0
-    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} FP64 RK4 steps of the N=1000 dimer (scipy CSR SpMV, one thread), "
-                      f"after the oracle's definition-route assembly ({asm_s:.1f} s)",
+    value = n / el
+    # one thread, scipy
+    v1 = SYS.initial_v(d)
+    eps = OP.eps_fn(p["E"], p["A"], p["omega"])
+    n1, el1 = 0, 0.0
+    t0 = time.perf_counter()
+    while n1 < 8 or el1 < 5.0:
+        v1, _ = OP.rk4(Q0, u.Q1, K, eps, v1, h, 4, t0=n1 * h)
+        n1 += 4
+        el1 = time.perf_counter() - t0
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} FP64 RK4 steps of the N=1000 dimer (the oracle's C RK4, rows shared over {threads} "
+                      f"OpenMP threads), after the oracle's definition-route assembly ({asm_s:.1f} s)",
+            "single_thread": {"value": n1 / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} steps with scipy's CSR product on one thread"},
             "assembly_s": asm_s}
 
 
@@ -310,6 +329,9 @@ def main():
     def step(prec=64):
         G.gksl_propagate(ctx, spp, STEP_RK4, prec, 0, 0, None)
 
+    # measured rates of this GPU (self-checking probes), outside the timed region
+    fma_rate, l2_rate = G.gksl_measure_rates(local)
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -346,11 +368,13 @@ def main():
                 "kernel": kernel + " (fused SpMV + RK4 stage update, FP64)"}
     # the co-limit: the FP64 pipe, against its rate at the SM clock sampled in the timed region
     ops = stage_fp64_ops(info.nnz_q0, D, info.long_rows, bool(info.q1_folded))
-    fp64_peak = fp64_peak_gops(ck["sm_mhz"] if ck else 2070.0)
+    fp64_peak = fma_rate / 1e9
     gops = ops / (avg_launch_ms * 1e-3) / 1e9
     roofline["fp64_pipe"] = {"ops_per_launch": ops, "achieved": gops, "peak": fp64_peak, "unit": "G FP64 ops/s",
                              "frac": gops / fp64_peak,
-                             "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x sampled SM clock"}
+                             "peak_kind": "measured: FP64 FMA chains checked against the host recurrence "
+                                          "(gksl_measure_rates), one op per FMA",
+                             "derived_peak_at_sampled_clock": fp64_peak_gops(ck["sm_mhz"] if ck else 2070.0)}
 
     # end to end through the C ABI with pinned host buffers: H2D of v, propagate, D2H of v
     host_in = torch.empty(D, dtype=torch.float64, pin_memory=True)
@@ -412,7 +436,12 @@ def main():
     G.gksl_destroy(ctx)
     if not args.no_extras and rank == 0:
         extras["matrix_free"] = matrix_free_extras(G, W, torch, stream, d, spp, args.steps)
-        extras.update(batched_and_adjoint(G, W, torch))
+        extras.update(batched_and_adjoint(G, W, torch, l2_rate))
+        extras.update(dense_and_asymptotic(G, W, torch))
+        extras["measured_rates"] = {"fp64_fma_per_s": fma_rate, "l2_read_gbs": l2_rate / 1e9,
+                                    "how": "gksl_measure_rates: FP64 FMA chains on 4 CTAs per SM checked bit for bit "
+                                           "against the host recurrence; 64 passes over a 32 MiB L2-resident buffer "
+                                           "read with ld.global.cg, sum checked"}
 
     if rank == 0:
         cpu = cpu_baseline_sample()
@@ -558,7 +587,18 @@ def run_profile_adjoint():
     G.gksl_destroy(ctx)
 
 
-def batched_and_adjoint(G, W, torch):
+def batch_group_bytes(D, B, entries):
+    """Bytes one FP32 RK4 step of a batched group moves through L2/L1, on the union path: per stage
+    every union entry's column and four channel values (20 B) once per tile, one 16-byte gather per
+    entry and active lane (4 B per entry and instance), and the stage updates' state traffic
+    (12 + 16 + 16 + 24 B per row and instance over the four stages).  Returns (L2-side bytes,
+    algorithmic bytes 4 (16 entries + 12 D B) of the workload statement)."""
+    l2 = 4 * (20 * entries + 4 * entries * B) + (12 + 16 + 16 + 24) * D * B
+    alg = 4 * (16 * entries + 12 * D * B)
+    return l2, alg
+
+
+def batched_and_adjoint(G, W, torch, l2_rate=None):
     """Side measurements: the batched form (256 seeded instances, N in {50, 100, 200}) and the
     adjoint gradient at N = 200 over period 20, each against the plain FP64 single-instance path."""
     out = {}
@@ -574,6 +614,7 @@ def batched_and_adjoint(G, W, torch):
     sec = G.gksl_batch_propagate(b, spps, steps, 0)
     inst_steps = sum(n * s for n, s in zip(n_inst, steps))
     tiles = [G.gksl_batch_info(b, i) for i in range(len(ctxs))]
+    stats = [G.gksl_batch_group_stats(b, i) for i in range(len(ctxs))]
     # error of the batched form (FP32 bulk, FP64 master) against the plain FP64 path: the first
     # instance of every group after the same steps, from the same state
     errors, first = [], 0
@@ -605,7 +646,23 @@ def batched_and_adjoint(G, W, torch):
         plain += (time.perf_counter() - t0) / n * s * ni
     for c in ctxs:
         G.gksl_destroy(c)
-    out["batched"] = {"instance_steps_per_s": inst_steps / sec, "instances": sum(n_inst),
+    # roofline of the group that bounds the run (the largest N, which runs the most steps): its
+    # per-step time alone (the autotuner's CUDA-event timing) against the measured L2 read rate
+    gi = len(stats) - 1
+    Dg, Bg, Ug = stats[gi]
+    l2b, algb = batch_group_bytes(Dg, Bg, Ug)
+    us = tiles[gi][1]
+    hbm, _ = peaks()
+    roof = None
+    if us > 0:
+        roof = {"bound": "l2", "group_N": sorted(groups)[gi], "rows": Dg, "instances": Bg, "union_entries": Ug,
+                "us_per_step": us, "l2_bytes_per_step": l2b, "achieved": l2b / (us * 1e-6) / 1e9,
+                "peak": (l2_rate / 1e9) if l2_rate else None, "unit": "GB/s",
+                "frac": (l2b / (us * 1e-6) / l2_rate) if l2_rate else None,
+                "peak_kind": "measured: L2-resident read rate (gksl_measure_rates)",
+                "algorithmic_bytes_per_step": algb, "algorithmic_gbs": algb / (us * 1e-6) / 1e9,
+                "algorithmic_frac_of_hbm": algb / (us * 1e-6) / 1e9 / hbm}
+    out["batched"] = {"instance_steps_per_s": inst_steps / sec, "instances": sum(n_inst), "roofline": roof,
                       "groups": {str(N): {"instances": n, "steps": s, "instances_per_lane": t[0], "tuned_us": t[1]}
                                  for N, n, s, t in zip(sorted(groups), n_inst, steps, tiles)},
                       "plain_fp64_instance_steps_per_s": inst_steps / plain if plain > 0 else None,
@@ -636,6 +693,74 @@ def batched_and_adjoint(G, W, torch):
         out["adjoint_plain_fp64_steps_per_s"] = S / (time.perf_counter() - t0)
     finally:
         G.gksl_destroy(c)
+    return out
+
+
+def dense_and_asymptotic(G, W, torch):
+    """Side measurements of the general-dissipator and asymptotic-state forms at N = 100:
+    assembly of a fully dense L and of a full-rank Kossakowski matrix (the dense route), RK4 on the
+    resulting 1e8-entry system, and the bifurcation scan over 32 interactions U with the paper's
+    transient of 10 periods."""
+    out = {}
+    N = 100
+    D = N * N - 1
+    H = W.random_operator(N, 0.05, 900, hermitian=True)
+    H1 = W.CSR.from_dense(np.diag(np.linspace(-1.0, 1.0, N)).astype(complex))
+    L = W.random_operator(N, 1.0, 901)
+    ctx = G.gksl_create(N)
+    try:
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 1.0, op=H)
+        G.set_csr_operator(G.gksl_set_h1, ctx, op=H1)
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, 0.02, op=L)
+        G.gksl_set_drive(ctx, 0.3, 0.5, 1.0)
+        G.gksl_assemble(ctx, 0)                 # warm-up (module loads, allocator)
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, 0.02, op=L)
+        sec = G.gksl_assemble(ctx, 0)
+        info = G.gksl_get_info(ctx)
+        re, im = W.random_density_matrix(N, 3, 902)
+        G.gksl_set_rho0(ctx, re, im)
+        spp = G.gksl_min_stable_steps(ctx)
+        G.gksl_propagate(ctx, spp, 16, 64, 0, 0, None)
+        torch.cuda.synchronize()
+        n = 64
+        t0 = time.perf_counter()
+        G.gksl_propagate(ctx, spp, n, 64, 0, 0, None)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        stage_bytes_dense = 12 * info.nnz_q0 + 17 * 8 * D / 4.0
+        out["dense_L_n100"] = {"assembly_s": sec, "nnz_R": info.nnz_r[0], "nnz_q0_plus_E_q1": info.nnz_q0,
+                               "rk4_steps_per_s": n / el,
+                               "stage_bytes": stage_bytes_dense, "stage_gbs": stage_bytes_dense * 4 * n / el / 1e9,
+                               "route": "dense (the sparse product would have about 5e9 terms)"}
+    finally:
+        G.gksl_destroy(ctx)
+    # full-rank Kossakowski matrix: c 1 + u u^+ (rank D, built in O(D^2) on the host)
+    rng = np.random.default_rng(5)
+    u = (rng.standard_normal(D) + 1j * rng.standard_normal(D)) / np.sqrt(2 * D)
+    A = np.outer(u, u.conj())
+    A[np.diag_indices(D)] += 0.05
+    ctx = G.gksl_create(N)
+    try:
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 1.0, op=H)
+        G.gksl_set_drive(ctx, 0.0, 0.0, 1.0)
+        t0 = time.perf_counter()
+        G.gksl_set_kossakowski(ctx, np.ascontiguousarray(A.real), np.ascontiguousarray(A.imag))
+        set_s = time.perf_counter() - t0
+        sec = G.gksl_assemble(ctx, 0)
+        info = G.gksl_get_info(ctx)
+        out["kossakowski_full_rank_n100"] = {"assembly_s": sec, "set_kossakowski_s": set_s,
+                                             "nnz_R": info.nnz_r[0], "rank": D}
+    finally:
+        G.gksl_destroy(ctx)
+    del A
+    # bifurcation scan: 32 values of U, transient 10 T, one more period for the residual
+    U = np.linspace(0.05, 1.0, 32)
+    t0 = time.perf_counter()
+    pops, spp, res, per = G.bifurcation_scan(N, U, transient=10, max_periods=1)
+    el = time.perf_counter() - t0
+    out["bifurcation_scan_n100"] = {"U_values": 32, "steps_per_period": spp, "periods": per,
+                                    "seconds_incl_assembly": el, "instance_steps_per_s": 32 * per * spp / el,
+                                    "max_period_residual": float(res.max()), "min_period_residual": float(res.min())}
     return out
 
 

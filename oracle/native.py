@@ -126,22 +126,33 @@ def _real_csr(X, D):
             np.ascontiguousarray(X.data, dtype=np.float64))
 
 
+class Rk4System:
+    """CSR arrays of dv/dt = (Q0 + eps(t) Q1) v + K prepared once for repeated ``run`` calls."""
+
+    def __init__(self, Q0, Q1, K, D):
+        self.D = D
+        self.q0 = _real_csr(Q0, D)
+        self.q1 = _real_csr(Q1, D) if Q1 is not None else (None, None, None)
+        self.K = None if K is None else np.ascontiguousarray(K, dtype=np.float64)
+
+    def run(self, E, A, omega, v0, h, nsteps, t0=0.0, emit_every=None, drive="sin"):
+        """Classical RK4 (Sec. IV step 3.1) from v0; returns (v_final, v every ``emit_every`` steps)."""
+        lib = _load_rk4()
+        D = self.D
+        v = np.array(v0, dtype=np.float64, copy=True)
+        ne = int(nsteps) // int(emit_every) if emit_every else 0
+        out = np.zeros((max(ne, 1), D))
+        st = lib.oracle_rk4(D, *[_p(x) for x in self.q0], *[_p(x) for x in self.q1], _p(self.K),
+                            0 if drive == "sin" else 1, float(E), float(A), float(omega), _p(v), float(t0), float(h),
+                            int(nsteps), int(emit_every or 0), _p(out))
+        if st != 0:
+            raise MemoryError("oracle_rk4: allocation failed")
+        return v, [out[i].copy() for i in range(ne)]
+
+
 def rk4(Q0, Q1, K, E, A, omega, v0, h, nsteps, t0=0.0, emit_every=None, drive="sin"):
     """Classical RK4 on dv/dt = (Q0 + eps(t) Q1) v + K (Sec. IV step 3.1) in C over all host
     cores: the same map as ``propagate.rk4`` with eps(t) = E + A sin(omega t) ("sin") or the
     square drive of ``propagate.eps_square_step`` ("square").  Q1, K may be None.
     Returns (v_final, list of v every ``emit_every`` steps)."""
-    lib = _load_rk4()
-    D = len(v0)
-    q0 = _real_csr(Q0, D)
-    q1 = _real_csr(Q1, D) if Q1 is not None else (None, None, None)
-    Kc = None if K is None else np.ascontiguousarray(K, dtype=np.float64)
-    v = np.array(v0, dtype=np.float64, copy=True)
-    ne = int(nsteps) // int(emit_every) if emit_every else 0
-    out = np.zeros((max(ne, 1), D))
-    st = lib.oracle_rk4(D, *[_p(x) for x in q0], *[_p(x) for x in q1], _p(Kc), 0 if drive == "sin" else 1,
-                        float(E), float(A), float(omega), _p(v), float(t0), float(h), int(nsteps),
-                        int(emit_every or 0), _p(out))
-    if st != 0:
-        raise MemoryError("oracle_rk4: allocation failed")
-    return v, [out[i].copy() for i in range(ne)]
+    return Rk4System(Q0, Q1, K, len(v0)).run(E, A, omega, v0, h, nsteps, t0=t0, emit_every=emit_every, drive=drive)

@@ -502,6 +502,11 @@ void merge(gksl_ctx *c, const std::vector<std::pair<const CsrR *, double>> &term
 
 }  // namespace
 
+void merge_terms(gksl_ctx *c, const std::vector<std::pair<const CsrR *, double>> &terms, const double *Kcol,
+                 CsrR &out) {
+    merge(c, terms, Kcol, 0.0, out, nullptr);
+}
+
 void csr_transpose(const CsrR &a, CsrR &t, cudaStream_t s) {
     DBuf<uint64_t> keys((size_t)(a.nnz > 0 ? a.nnz : 1));
     DBuf<double> vals((size_t)(a.nnz > 0 ? a.nnz : 1));

@@ -89,6 +89,9 @@ void build_hyb_multi(const std::vector<const CsrR *> &ms, const std::vector<doub
                      const std::vector<Hyb<double> *> &out, const std::vector<Hyb<float> *> &outf, cudaStream_t s);
 
 // CSR helpers (assemble.cu)
+// sum_i w_i M_i (+ Kcol as column D when given) -> CSR without exact zeros, on the context's stream
+void merge_terms(gksl_ctx *c, const std::vector<std::pair<const CsrR *, double>> &terms, const double *Kcol,
+                 CsrR &out);
 void csr_transpose(const CsrR &a, CsrR &t, cudaStream_t s);
 void csr_copy_out(gksl_ctx *c, const CsrR &m, long long *nnz, int *rowptr, int *col, double *val);
 

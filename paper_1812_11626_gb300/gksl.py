@@ -91,6 +91,7 @@ _SIGS = {
     "gksl_batch_get_state": (_S, [_P, _I, _P]),
     "gksl_batch_info": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "gksl_batch_set_scan": (_S, [_P, _I, _P]),
+    "gksl_batch_group_stats": (_S, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_I), ctypes.POINTER(_L)]),
     "gksl_batch_asymptotic": (_S, [_P, _P, _L, _L, _D, _L, _P, ctypes.POINTER(_L)]),
     "gksl_get_info": (_S, [_P, ctypes.POINTER(gksl_info)]),
     "gksl_measure_rates": (_S, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -319,6 +320,14 @@ def gksl_batch_asymptotic(b, steps_per_period, transient, max_periods, tol, corr
     _check(_lib.gksl_batch_asymptotic(b, _ptr(spp), int(transient), int(max_periods), float(tol),
                                       int(correction_every), _ptr(res), ctypes.byref(per)), batch=b)
     return res, per.value
+
+
+def gksl_batch_group_stats(b, group):
+    """(rows D, instances, union-pattern entries) of one group."""
+    rows, inst, ent = _L(), _I(), _L()
+    _check(_lib.gksl_batch_group_stats(b, int(group), ctypes.byref(rows), ctypes.byref(inst), ctypes.byref(ent)),
+           batch=b)
+    return rows.value, inst.value, ent.value
 
 
 def gksl_batch_info(b, group):

@@ -16,7 +16,13 @@ def G():
     return gksl
 
 
-def test_batch_mixed_n_vs_oracle(G):
+@pytest.mark.parametrize("tile", ["auto", "0", "1", "3"])
+def test_batch_mixed_n_vs_oracle(G, tile, monkeypatch):
+    """Mixed N in one batch, every instance path: the autotuner's choice, the 16-byte-gather path on
+    the union pattern (tile 0, shared-memory staging) and the scalar paths with 1 and 3 instances
+    per lane, each against per-instance oracle runs."""
+    if tile != "auto":
+        monkeypatch.setenv("GKSL_BATCH_TILE", tile)
     sizes = [(5, 3), (9, 40), (12, 70)]   # (N, instances): chunk widths 1..3 warps of lanes
     rng = np.random.default_rng(3)
     ctxs, A, g, inst = [], [], [], []
@@ -79,10 +85,14 @@ def test_batch_256_seeded_instances_sampled(G, record):
             G.gksl_destroy(c)
 
 
-def test_bifurcation_scan_vs_oracle(G):
+@pytest.mark.parametrize("tile", ["auto", "0", "2"])
+def test_bifurcation_scan_vs_oracle(G, tile, monkeypatch):
     """U-scan of the dimer as one batch (a per-instance interaction weight): populations
     diag rho after 2 periods for 8 values of U against single-instance oracle runs, and the
-    populations are a probability distribution."""
+    populations are a probability distribution; with the scanned component as the fourth value
+    channel of the union pattern (tile 0) and of the scalar path (tile 2)."""
+    if tile != "auto":
+        monkeypatch.setenv("GKSL_BATCH_TILE", tile)
     N = 12
     U = np.linspace(0.0, 1.4, 8)
     pops, spp, res, per = G.bifurcation_scan(N, U, transient=1, max_periods=1)
