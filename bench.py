@@ -587,14 +587,15 @@ def run_profile_adjoint():
     G.gksl_destroy(ctx)
 
 
-def batch_group_bytes(D, B, entries):
-    """Bytes one FP32 RK4 step of a batched group moves through L2/L1, on the union path: per stage
-    every union entry's column and four channel values (20 B) once per tile, one 16-byte gather per
-    entry and active lane (4 B per entry and instance), and the stage updates' state traffic
-    (12 + 16 + 16 + 24 B per row and instance over the four stages).  Returns (L2-side bytes,
-    algorithmic bytes 4 (16 entries + 12 D B) of the workload statement)."""
-    l2 = 4 * (20 * entries + 4 * entries * B) + (12 + 16 + 16 + 24) * D * B
-    alg = 4 * (16 * entries + 12 * D * B)
+def batch_group_bytes(D, B, entries, nnz_union):
+    """Bytes one FP32 RK4 step of a batched group moves through L2/L1: per stage and instance chunk
+    every stored channel entry's column and value (8 B, read by the whole warp), one 4-byte gather
+    per entry and instance, and the stage updates' state traffic (12 + 16 + 16 + 24 B per row and
+    instance over the four stages).  Returns (L2-side bytes, algorithmic bytes
+    4 (16 nnz_union + 12 D B) of the workload statement, nnz_union the union pattern of the
+    channels)."""
+    l2 = 4 * (8 * entries + 4 * entries * B) + (12 + 16 + 16 + 24) * D * B
+    alg = 4 * (16 * nnz_union + 12 * D * B)
     return l2, alg
 
 
@@ -615,6 +616,7 @@ def batched_and_adjoint(G, W, torch, l2_rate=None):
     inst_steps = sum(n * s for n, s in zip(n_inst, steps))
     tiles = [G.gksl_batch_info(b, i) for i in range(len(ctxs))]
     stats = [G.gksl_batch_group_stats(b, i) for i in range(len(ctxs))]
+    nnz_union = [G.gksl_get_info(c).nnz_q0 for c in ctxs]   # [Q0 + E Q1 | K] of each group's context
     # error of the batched form (FP32 bulk, FP64 master) against the plain FP64 path: the first
     # instance of every group after the same steps, from the same state
     errors, first = [], 0
@@ -650,12 +652,12 @@ def batched_and_adjoint(G, W, torch, l2_rate=None):
     # per-step time alone (the autotuner's CUDA-event timing) against the measured L2 read rate
     gi = len(stats) - 1
     Dg, Bg, Ug = stats[gi]
-    l2b, algb = batch_group_bytes(Dg, Bg, Ug)
+    l2b, algb = batch_group_bytes(Dg, Bg, Ug, nnz_union[gi])
     us = tiles[gi][1]
     hbm, _ = peaks()
     roof = None
     if us > 0:
-        roof = {"bound": "l2", "group_N": sorted(groups)[gi], "rows": Dg, "instances": Bg, "union_entries": Ug,
+        roof = {"bound": "l2", "group_N": sorted(groups)[gi], "rows": Dg, "instances": Bg, "channel_entries": Ug,
                 "us_per_step": us, "l2_bytes_per_step": l2b, "achieved": l2b / (us * 1e-6) / 1e9,
                 "peak": (l2_rate / 1e9) if l2_rate else None, "unit": "GB/s",
                 "frac": (l2b / (us * 1e-6) / l2_rate) if l2_rate else None,

@@ -270,17 +270,17 @@ gksl_status gksl_batch_asymptotic(gksl_batch *b, const long long *steps_per_peri
 /* State of instance i (D_i doubles, FP64 master). */
 gksl_status gksl_batch_get_state(gksl_batch *b, int instance, double *v);
 /* Tile width chosen by the autotuner for group `group` (instances per lane; one warp covers
- * 32 * instances_per_lane instances of a row; 4 also for the 16-byte-gather path on the union
- * pattern of the channels, which stages each 8-row tile's entries in shared memory) and its timed
+ * 32 * instances_per_lane instances of a row; 4 also for the path with one 16-byte gather of 4
+ * instances per lane and entry) and its timed
  * cost per FP32 step in microseconds.  Both are 0 before the first gksl_batch_propagate.  The
  * environment variable GKSL_BATCH_TILE=0 forces the 16-byte-gather path, 1..4 the scalar path with
  * that many instances per lane (no timing; the cost is then reported as 0). */
 gksl_status gksl_batch_info(gksl_batch *b, int group, int *instances_per_lane, double *tuned_us_per_step);
-/* Size of group `group`: rows D, instances, and the stored entries of the union pattern of its
- * value channels (QH, Q1, [R | K] and a scanned component; one column per entry), which the
- * 16-byte-gather path streams once per stage and instance chunk.  Any pointer may be NULL. */
+/* Size of group `group`: rows D, instances, and the stored entries of its value channels summed
+ * (QH, Q1, [R | K] and a scanned component), which a stage streams once per instance chunk.
+ * Any pointer may be NULL. */
 gksl_status gksl_batch_group_stats(gksl_batch *b, int group, long long *rows, int *instances,
-                                   long long *union_entries);
+                                   long long *channel_entries);
 
 /* ------------------------------------------------------------------ allocation-free propagation */
 

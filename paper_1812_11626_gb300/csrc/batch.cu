@@ -34,14 +34,8 @@ constexpr int kMaxGroups = 8;
 constexpr int kBatchGraphSteps = 32;
 
 constexpr int kMaxCh = 4;   // QH, Q1, [R | K], and optionally one scanned Hamiltonian component
-constexpr int kPiece = 512; // union entries a CTA stages in shared memory at a time (10 KB)
 
 struct GroupDev {
-    // union of the channels' patterns (one column per entry, the channel values as one float4:
-    // QH, Q1, [R | K], scanned component), read by the FP32 16-byte-gather path
-    const int *uptr;
-    const int *ucol;
-    const float4 *uval;
     const int *ptr[kMaxCh];
     const int *col[kMaxCh];
     const float *vf[kMaxCh];
@@ -170,67 +164,50 @@ __device__ inline void row_scalar(const GroupDev &G, long long r, int ch, int la
     }
 }
 
-// One tile (8 consecutive rows r0.., instances ch * 128 + [0, 128)) of the FP32 path on the union
-// pattern.  The tile's entries are contiguous in the union CSR; the CTA stages them in shared
-// memory kPiece at a time with coalesced loads, so a warp's chain per entry is a shared-memory
-// read followed by its 16-byte gather V[col, 4 lane .. 4 lane + 3] (4 instances per lane).  Every
-// thread of the CTA takes part in the staging and the barriers, including lanes without
-// instances and warps without a row.
+// Row r for 4 consecutive instances per lane (128 per warp), one 16-byte gather per entry.
 template <int STAGE>
-__device__ inline void tile_union(const GroupDev &G, long long r0, int ch, int warp, int lane, long long step,
-                                  int *s_col, float4 *s_val) {
-    const long long Bs = G.Bs;
+__device__ inline void row_vec4(const GroupDev &G, long long r, int ch, int lane, long long step) {
     const int bq = ch * 128 + 4 * lane;
-    const bool act = bq < G.B;
+    if (bq >= G.B) return;
+    const long long Bs = G.Bs;
     const float *X = STAGE == 1 ? G.V32 : (STAGE == 3 ? G.Y32[1] : G.Y32[0]);
-    const long long rows = G.D - r0 < kRowsPerTile ? G.D - r0 : kRowsPerTile;
-    const long long r = r0 + warp;
-    const bool has_row = warp < rows;
-    const int e0 = G.uptr[r0], e1 = G.uptr[r0 + rows];
-    const int ea = has_row ? G.uptr[r] : 0, eb = has_row ? G.uptr[r + 1] : 0;
-    const bool scan = G.nch > 3;
     float4 acc[kMaxCh];
 #pragma unroll
     for (int c = 0; c < kMaxCh; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int p0 = e0; p0 < e1; p0 += kPiece) {
-        const int pn = e1 - p0 < kPiece ? e1 - p0 : kPiece;
-        __syncthreads();   // the previous piece (or tile) has been read
-        for (int i = threadIdx.x; i < pn; i += blockDim.x) {
-            s_col[i] = G.ucol[p0 + i];
-            s_val[i] = G.uval[p0 + i];
-        }
-        __syncthreads();
-        const int lo = (ea > p0 ? ea : p0) - p0, hi = (eb < p0 + pn ? eb : p0 + pn) - p0;
-        if (!act) continue;
-        constexpr int U = 4;
-        int e = lo;
-        for (; e + U <= hi; e += U) {
+    constexpr int U = 4;
+#pragma unroll
+    for (int c = 0; c < kMaxCh; ++c) {
+        if (c >= G.nch) break;
+        const int e1 = G.ptr[c][r + 1];
+        int e = G.ptr[c][r];
+        for (; e + U <= e1; e += U) {
+            int col[U];
+            float v[U];
             float4 x[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) x[u] = __ldg((const float4 *)(X + (long long)s_col[e + u] * Bs + bq));
+            for (int u = 0; u < U; ++u) {
+                col[u] = G.col[c][e + u];
+                v[u] = G.vf[c][e + u];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) x[u] = __ldg((const float4 *)(X + (long long)col[u] * Bs + bq));
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const float4 w = s_val[e + u];
-                acc[0].x += w.x * x[u].x; acc[0].y += w.x * x[u].y; acc[0].z += w.x * x[u].z; acc[0].w += w.x * x[u].w;
-                acc[1].x += w.y * x[u].x; acc[1].y += w.y * x[u].y; acc[1].z += w.y * x[u].z; acc[1].w += w.y * x[u].w;
-                acc[2].x += w.z * x[u].x; acc[2].y += w.z * x[u].y; acc[2].z += w.z * x[u].z; acc[2].w += w.z * x[u].w;
-                if (scan) {
-                    acc[3].x += w.w * x[u].x; acc[3].y += w.w * x[u].y; acc[3].z += w.w * x[u].z; acc[3].w += w.w * x[u].w;
-                }
+                acc[c].x += v[u] * x[u].x;
+                acc[c].y += v[u] * x[u].y;
+                acc[c].z += v[u] * x[u].z;
+                acc[c].w += v[u] * x[u].w;
             }
         }
-        for (; e < hi; ++e) {
-            const float4 x = __ldg((const float4 *)(X + (long long)s_col[e] * Bs + bq));
-            const float4 w = s_val[e];
-            acc[0].x += w.x * x.x; acc[0].y += w.x * x.y; acc[0].z += w.x * x.z; acc[0].w += w.x * x.w;
-            acc[1].x += w.y * x.x; acc[1].y += w.y * x.y; acc[1].z += w.y * x.z; acc[1].w += w.y * x.w;
-            acc[2].x += w.z * x.x; acc[2].y += w.z * x.y; acc[2].z += w.z * x.z; acc[2].w += w.z * x.w;
-            if (scan) {
-                acc[3].x += w.w * x.x; acc[3].y += w.w * x.y; acc[3].z += w.w * x.z; acc[3].w += w.w * x.w;
-            }
+        for (; e < e1; ++e) {
+            const float v = G.vf[c][e];
+            const float4 x = __ldg((const float4 *)(X + (long long)G.col[c][e] * Bs + bq));
+            acc[c].x += v * x.x;
+            acc[c].y += v * x.y;
+            acc[c].z += v * x.z;
+            acc[c].w += v * x.w;
         }
     }
-    if (!has_row || !act) return;
     const int slot = STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1);
     const float sn = G.sin_tab_f[3 * step + slot];
     const float a0[4] = {acc[0].x, acc[0].y, acc[0].z, acc[0].w};
@@ -242,18 +219,13 @@ __device__ inline void tile_union(const GroupDev &G, long long r0, int ch, int w
         int b = bq + k;
         if (b >= G.B) break;
         float kf = a0[k] + (G.Af[b] * sn) * a1[k] + G.gf[b] * a2[k];
-        if (scan) kf += G.Sf[b] * a3[k];
+        if (G.nch > 3) kf += G.Sf[b] * a3[k];
         stage_update<STAGE, false>(G, r * Bs + b, 0.0, kf);
     }
 }
 
-// One launch per RK4 stage over every group: a CTA walks tiles (group, 8 rows, instance chunk);
-// FP32 steps of groups on the 16-byte-gather path take the tile as a CTA (tile_union), the
-// others give each warp one row of it.
 template <int STAGE, bool F64>
-__global__ void __launch_bounds__(kBThreads, 4) k_batch_stage(BatchArgs a) {
-    __shared__ int s_col[kPiece];
-    __shared__ float4 s_val[kPiece];
+__global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
     const long long step = *a.base + a.local;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -261,16 +233,12 @@ __global__ void __launch_bounds__(kBThreads, 4) k_batch_stage(BatchArgs a) {
         while (gi + 1 < a.ng && t >= a.gr[gi + 1].tile_begin) ++gi;
         const GroupDev &G = a.gr[gi];
         if (step >= G.nsteps) continue;
-        const long long tl = t - G.tile_begin;
-        const long long r0 = (tl / G.nchunks) * kRowsPerTile;
-        const int ch = (int)(tl % G.nchunks);
-        if (!F64 && G.vec4) {
-            tile_union<STAGE>(G, r0, ch, warp, lane, step, s_col, s_val);
-            continue;
-        }
-        const long long r = r0 + warp;
+        long long tl = t - G.tile_begin;
+        long long r = (tl / G.nchunks) * kRowsPerTile + warp;
+        int ch = (int)(tl % G.nchunks);
         if (r >= G.D) continue;
-        row_scalar<STAGE, F64>(G, r, ch, lane, step);
+        if (!F64 && G.vec4) row_vec4<STAGE>(G, r, ch, lane, step);
+        else row_scalar<STAGE, F64>(G, r, ch, lane, step);
     }
 }
 
@@ -339,9 +307,6 @@ struct Group {
     double h = 0.0;
     double t = 0.0;   // time of the group's states
     double tuned_us = 0.0;
-    DBuf<int> uptr, ucol;               // union pattern of the channels (FP32 16-byte-gather path)
-    DBuf<float4> uval;
-    long long unnz = 0;
     DBuf<double> Vprev;                 // state one period earlier (gksl_batch_asymptotic)
     DBuf<unsigned long long> resid;     // per-instance period-map residual, as double bit patterns
 };
@@ -377,79 +342,6 @@ __global__ void k_f2(const double *__restrict__ v, float *__restrict__ o, long l
     if (i < n) o[i] = (float)v[i];
 }
 
-// Union pattern of a group's channels, row by row: a merge of the channels' sorted column lists
-// (one thread per row; rows hold at most N + 10 entries).  Pass 1 counts a row's distinct
-// columns, pass 2 writes them with each channel's FP32 value (0 where a channel has none).
-struct ChanCsr {
-    const int *ptr[kMaxCh];
-    const int *col[kMaxCh];
-    const float *val[kMaxCh];
-    int nch;
-};
-
-template <bool FILL>
-__global__ void k_union_rows(ChanCsr m, long long D, long long *__restrict__ cnt, const int *__restrict__ uptr,
-                             int *__restrict__ ucol, float4 *__restrict__ uval) {
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= D) return;
-    int e[kMaxCh], end[kMaxCh];
-    for (int c = 0; c < kMaxCh; ++c) {
-        e[c] = c < m.nch ? m.ptr[c][r] : 0;
-        end[c] = c < m.nch ? m.ptr[c][r + 1] : 0;
-    }
-    int n = 0;
-    long long o = FILL ? uptr[r] : 0;
-    for (;;) {
-        int cmin = 0x7fffffff;
-        for (int c = 0; c < m.nch; ++c)
-            if (e[c] < end[c] && m.col[c][e[c]] < cmin) cmin = m.col[c][e[c]];
-        if (cmin == 0x7fffffff) break;
-        float v[kMaxCh] = {0.f, 0.f, 0.f, 0.f};
-        for (int c = 0; c < m.nch; ++c)
-            if (e[c] < end[c] && m.col[c][e[c]] == cmin) {
-                if (FILL) v[c] = m.val[c][e[c]];
-                ++e[c];
-            }
-        if (FILL) {
-            ucol[o] = cmin;
-            uval[o] = make_float4(v[0], v[1], v[2], v[3]);
-            ++o;
-        }
-        ++n;
-    }
-    if (!FILL) cnt[r] = n;
-}
-
-__global__ void k_int_from_ll(const long long *__restrict__ in, long long n, int *__restrict__ out) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (int)in[i];
-}
-
-void build_union(Group &G, cudaStream_t s) {
-    ChanCsr m{};
-    m.nch = G.nch;
-    for (int c = 0; c < G.nch; ++c) {
-        m.ptr[c] = G.m[c].rowptr.p;
-        m.col[c] = G.m[c].col.p;
-        m.val[c] = G.mf[c].p;
-    }
-    const long long D = G.D;
-    DBuf<long long> cnt((size_t)D), off((size_t)D + 1);
-    k_union_rows<false><<<grid_for(D, 256), 256, 0, s>>>(m, D, cnt.p, nullptr, nullptr, nullptr);
-    GK_LAUNCH_CHECK();
-    const long long nnz = scan_ll(cnt.p, off.p, D, true, true, s);
-    GK_REQUIRE(nnz < (1LL << 31), GKSL_ERR_ARG, "batched group has more than 2^31 - 1 stored entries");
-    G.uptr.alloc((size_t)D + 1);
-    G.ucol.alloc((size_t)std::max(1LL, nnz));
-    G.uval.alloc((size_t)std::max(1LL, nnz));
-    k_int_from_ll<<<grid_for(D + 1, 256), 256, 0, s>>>(off.p, D + 1, G.uptr.p);
-    GK_LAUNCH_CHECK();
-    k_union_rows<true><<<grid_for(D, 256), 256, 0, s>>>(m, D, nullptr, G.uptr.p, G.ucol.p, G.uval.p);
-    GK_LAUNCH_CHECK();
-    G.unnz = nnz;
-    GK_CUDA(cudaStreamSynchronize(s));
-}
-
 BatchArgs make_args(gksl_batch *b, bool f64, long long local) {
     BatchArgs a{};
     a.ng = (int)b->groups.size();
@@ -457,9 +349,6 @@ BatchArgs make_args(gksl_batch *b, bool f64, long long local) {
     for (int i = 0; i < a.ng; ++i) {
         Group &G = b->groups[i];
         GroupDev &d = a.gr[i];
-        d.uptr = G.uptr.p;
-        d.ucol = G.ucol.p;
-        d.uval = G.uval.p;
         for (int c = 0; c < kMaxCh; ++c) {
             d.ptr[c] = G.m[c].rowptr.p;
             d.col[c] = G.m[c].col.p;
@@ -587,7 +476,7 @@ void reset_batch(gksl_batch *b) {
 void autotune(gksl_batch *b) {
     std::vector<Group *> all;
     for (auto &G : b->groups) all.push_back(&G);
-    // GKSL_BATCH_TILE=0 forces the 16-byte-gather union path, 1..4 the scalar path with that many
+    // GKSL_BATCH_TILE=0 forces the 16-byte-gather path, 1..4 the scalar path with that many
     // instances per lane (for tests of each path; normally chosen by timing)
     const char *env = getenv("GKSL_BATCH_TILE");
     if (env && env[0] >= '0' && env[0] <= '0' + kMaxIpl && env[1] == 0) {
@@ -727,7 +616,6 @@ extern "C" gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, 
                 }
             }
             GK_CUDA(cudaStreamSynchronize(s));
-            build_union(G, s);
             G.A.alloc((size_t)G.B);
             G.g.alloc((size_t)G.B);
             G.Af.alloc((size_t)G.B);
@@ -978,7 +866,6 @@ extern "C" gksl_status gksl_batch_set_scan(gksl_batch *b, int component, const d
             GK_CUDA(cudaMemcpy(G.S.p, s.data(), sizeof(double) * G.B, cudaMemcpyHostToDevice));
             GK_CUDA(cudaMemcpy(G.Sf.p, sf.data(), sizeof(float) * G.B, cudaMemcpyHostToDevice));
             G.nch = 4;
-            build_union(G, b->stream);
         }
         GK_CUDA(cudaStreamSynchronize(b->stream));
         clear_batch_graphs(b);
@@ -987,13 +874,17 @@ extern "C" gksl_status gksl_batch_set_scan(gksl_batch *b, int component, const d
 }
 
 extern "C" gksl_status gksl_batch_group_stats(gksl_batch *b, int group, long long *rows, int *instances,
-                                              long long *union_entries) {
+                                              long long *channel_entries) {
     return bguarded(b, [&] {
         GK_REQUIRE(group >= 0 && group < (int)b->groups.size(), GKSL_ERR_ARG, "bad group");
         const Group &G = b->groups[group];
         if (rows) *rows = G.D;
         if (instances) *instances = G.B;
-        if (union_entries) *union_entries = G.unnz;
+        if (channel_entries) {
+            long long n = 0;
+            for (int c = 0; c < G.nch; ++c) n += G.m[c].nnz;
+            *channel_entries = n;
+        }
     });
 }
 

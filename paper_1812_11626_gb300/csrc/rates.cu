@@ -38,19 +38,30 @@ __global__ void __launch_bounds__(256) k_fma_chains(long long iters, double a, d
 }
 
 // Sum of `reps` passes over an L2-resident buffer of n float4 (every component 1.0), read with
-// ld.global.cg (cached in L2, not in L1); each thread adds its 4-float sums into one double.
+// ld.global.cg (cached in L2, not in L1).  Each thread keeps four independent loads in flight
+// (elements i, i + S, i + 2S, i + 3S of a pass with grid stride S) and four float partial sums,
+// which stay exact (small integers); the double total is exact as well.
 __global__ void __launch_bounds__(256) k_l2_read(const float4 *__restrict__ buf, long long n, int reps,
                                                   double *__restrict__ total) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    float s = 0.0f;
+    const long long S = (long long)gridDim.x * blockDim.x;
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double acc = 0.0;
     for (int r = 0; r < reps; ++r) {
-        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-            float4 v = __ldcg(buf + i);
-            s += (v.x + v.y) + (v.z + v.w);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        long long i = i0;
+        for (; i + 3 * S < n; i += 4 * S) {
+            const float4 a = __ldcg(buf + i), b = __ldcg(buf + i + S), c = __ldcg(buf + i + 2 * S),
+                         d = __ldcg(buf + i + 3 * S);
+            s0 += (a.x + a.y) + (a.z + a.w);
+            s1 += (b.x + b.y) + (b.z + b.w);
+            s2 += (c.x + c.y) + (c.z + c.w);
+            s3 += (d.x + d.y) + (d.z + d.w);
         }
-        acc += s;   // exact: each pass adds at most n / stride * 4 units to a float below 2^24
-        s = 0.0f;
+        for (; i < n; i += S) {
+            const float4 a = __ldcg(buf + i);
+            s0 += (a.x + a.y) + (a.z + a.w);
+        }
+        acc += (double)s0 + (double)s1 + (double)s2 + (double)s3;
     }
     atomicAdd(total, acc);
 }
@@ -120,7 +131,7 @@ extern "C" gksl_status gksl_measure_rates(int device, double *fp64_fma_per_s, do
             DBuf<double> total(1);
             k_fill_ones<<<grid_for(n, 256), 256>>>(buf.p, n);
             GK_LAUNCH_CHECK();
-            const unsigned grid = (unsigned)sms * 8;
+            const unsigned grid = (unsigned)sms * 4;
             for (int pass = 0; pass < 2; ++pass) {   // the first pass warms the L2
                 GK_CUDA(cudaMemset(total.p, 0, sizeof(double)));
                 GK_CUDA(cudaEventRecord(e0));

@@ -323,7 +323,7 @@ def gksl_batch_asymptotic(b, steps_per_period, transient, max_periods, tol, corr
 
 
 def gksl_batch_group_stats(b, group):
-    """(rows D, instances, union-pattern entries) of one group."""
+    """(rows D, instances, stored entries summed over the value channels) of one group."""
     rows, inst, ent = _L(), _I(), _L()
     _check(_lib.gksl_batch_group_stats(b, int(group), ctypes.byref(rows), ctypes.byref(inst), ctypes.byref(ent)),
            batch=b)

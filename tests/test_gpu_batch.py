@@ -49,7 +49,10 @@ def test_batch_mixed_n_vs_oracle(G, tile, monkeypatch):
             assert np.abs(v - v_ref).max() < 1e-5, (i, N, np.abs(v - v_ref).max())
         for gi in range(len(sizes)):
             ipl, us = G.gksl_batch_info(b, gi)
-            assert 1 <= ipl <= 4 and us > 0
+            if tile == "auto":
+                assert 1 <= ipl <= 4 and us > 0
+            else:   # forced: no timing, the forced width (4 for the 16-byte path)
+                assert ipl == (4 if tile == "0" else int(tile)) and us == 0
     finally:
         G.gksl_batch_destroy(b)
         for c in ctxs:
