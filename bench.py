@@ -277,6 +277,8 @@ def main():
                     help="profiling case for ncu: N=1000 assembly, then 50 FP64 and 50 FP32 RK4 steps")
     ap.add_argument("--profile-mf", action="store_true",
                     help="profiling case for ncu: the N=1000 matrix-free form, 20 FP64 and 20 FP32 RK4 steps")
+    ap.add_argument("--profile-dense", action="store_true",
+                    help="profiling case for ncu: assembly of a dense L at N=100 (the dense dissipator route)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="profiling case for ncu: the 256-instance batch, 40 steps per group")
     ap.add_argument("--profile-adjoint", action="store_true",
@@ -289,6 +291,9 @@ def main():
         return
     if args.profile:
         run_profile_case()
+        return
+    if args.profile_dense:
+        run_profile_dense()
         return
     if args.profile_batch:
         run_profile_batch()
@@ -540,6 +545,23 @@ def run_profile_case():
     info = G.gksl_get_info(ctx)
     print(json.dumps({"profile_case": "N=1000", "nnz_q0": info.nnz_q0, "nnz_q1": info.nnz_q1, "D": info.D,
                       "src_hash": src_hash(), "steps_per_period": spp}), flush=True)
+    G.gksl_destroy(ctx)
+
+
+def run_profile_dense():
+    """Small, fixed case for ncu: one assembly of a fully dense L at N = 100, which takes the dense
+    dissipator route (k_dense_R twice over the 1e8 entries of R: count, then fill)."""
+    import torch
+    from paper_1812_11626_gb300 import gksl as G, workloads as W
+    N = 100
+    ctx = G.gksl_create(N)
+    G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 1.0, op=W.random_operator(N, 0.05, 900, hermitian=True))
+    G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, 0.02, op=W.random_operator(N, 1.0, 901))
+    G.gksl_set_drive(ctx, 0.0, 0.0, 1.0)
+    sec = G.gksl_assemble(ctx, 0)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "dense L N=100", "assembly_s": sec, "nnz_r": G.gksl_get_info(ctx).nnz_r[0]}),
+          flush=True)
     G.gksl_destroy(ctx)
 
 
