@@ -609,16 +609,21 @@ def run_profile_adjoint():
     G.gksl_destroy(ctx)
 
 
-def batch_group_bytes(D, B, entries, nnz_union):
-    """Bytes one FP32 RK4 step of a batched group moves through L2/L1: per stage and instance chunk
-    every stored channel entry's column and value (8 B, read by the whole warp), one 4-byte gather
-    per entry and instance, and the stage updates' state traffic (12 + 16 + 16 + 24 B per row and
-    instance over the four stages).  Returns (L2-side bytes, algorithmic bytes
-    4 (16 nnz_union + 12 D B) of the workload statement, nnz_union the union pattern of the
-    channels)."""
-    l2 = 4 * (8 * entries + 4 * entries * B) + (12 + 16 + 16 + 24) * D * B
+def batch_group_bytes(D, B, entries, pair_entries, path, nnz_union):
+    """Bytes one FP32 RK4 step of a batched group requests from L1/L2: per stage and instance chunk
+    every stored entry's column and values (row paths: 8 B per channel entry; pair path: 4 B of
+    column and two float4 of channel values, 36 B, per pair-unit entry), one 4-byte gather per
+    entry and instance (channel entries on rows, pair-unit entries on pairs), and the stage
+    updates' state traffic (12 + 16 + 16 + 24 B per row and instance over the four stages).
+    Returns (requested bytes, algorithmic bytes 4 (16 nnz_union + 12 D B) of the workload
+    statement, nnz_union the union pattern of the channels)."""
+    if path == 2:
+        req = 4 * (36 * pair_entries + 4 * pair_entries * B)
+    else:
+        req = 4 * (8 * entries + 4 * entries * B)
+    req += (12 + 16 + 16 + 24) * D * B
     alg = 4 * (16 * nnz_union + 12 * D * B)
-    return l2, alg
+    return req, alg
 
 
 def batched_and_adjoint(G, W, torch, l2_rate=None):
@@ -673,22 +678,25 @@ def batched_and_adjoint(G, W, torch, l2_rate=None):
     # roofline of the group that bounds the run (the largest N, which runs the most steps): its
     # per-step time alone (the autotuner's CUDA-event timing) against the measured L2 read rate
     gi = len(stats) - 1
-    Dg, Bg, Ug = stats[gi]
-    l2b, algb = batch_group_bytes(Dg, Bg, Ug, nnz_union[gi])
+    Dg, Bg, Ug, Pg, path = stats[gi]
+    l2b, algb = batch_group_bytes(Dg, Bg, Ug, Pg, path, nnz_union[gi])
     us = tiles[gi][1]
     hbm, _ = peaks()
     roof = None
     if us > 0:
         roof = {"bound": "l2", "group_N": sorted(groups)[gi], "rows": Dg, "instances": Bg, "channel_entries": Ug,
-                "us_per_step": us, "l2_bytes_per_step": l2b, "achieved": l2b / (us * 1e-6) / 1e9,
+                "pair_unit_entries": Pg, "path": ["16-byte rows", "scalar rows", "pair units"][path],
+                "us_per_step": us, "requested_bytes_per_step": l2b, "achieved": l2b / (us * 1e-6) / 1e9,
                 "peak": (l2_rate / 1e9) if l2_rate else None, "unit": "GB/s",
                 "frac": (l2b / (us * 1e-6) / l2_rate) if l2_rate else None,
-                "peak_kind": "measured: L2-resident read rate (gksl_measure_rates)",
+                "peak_kind": "measured: L2-resident read rate (gksl_measure_rates); achieved counts the bytes the "
+                             "kernel requests from L1/L2, some of which L1 serves",
                 "algorithmic_bytes_per_step": algb, "algorithmic_gbs": algb / (us * 1e-6) / 1e9,
                 "algorithmic_frac_of_hbm": algb / (us * 1e-6) / 1e9 / hbm}
     out["batched"] = {"instance_steps_per_s": inst_steps / sec, "instances": sum(n_inst), "roofline": roof,
-                      "groups": {str(N): {"instances": n, "steps": s, "instances_per_lane": t[0], "tuned_us": t[1]}
-                                 for N, n, s, t in zip(sorted(groups), n_inst, steps, tiles)},
+                      "groups": {str(N): {"instances": n, "steps": s, "instances_per_lane": t[0], "tuned_us": t[1],
+                                          "path": ["16-byte rows", "scalar rows", "pair units"][st[4]]}
+                                 for N, n, s, t, st in zip(sorted(groups), n_inst, steps, tiles, stats)},
                       "plain_fp64_instance_steps_per_s": inst_steps / plain if plain > 0 else None,
                       "error_vs_plain_fp64": errors}
     # adjoint at N = 200: gradient of the mean of <n1 - n2> over period 20 at the stable step

@@ -273,14 +273,19 @@ gksl_status gksl_batch_get_state(gksl_batch *b, int instance, double *v);
  * 32 * instances_per_lane instances of a row; 4 also for the path with one 16-byte gather of 4
  * instances per lane and entry) and its timed
  * cost per FP32 step in microseconds.  Both are 0 before the first gksl_batch_propagate.  The
- * environment variable GKSL_BATCH_TILE=0 forces the 16-byte-gather path, 1..4 the scalar path with
- * that many instances per lane (no timing; the cost is then reported as 0). */
+ * autotuner also times each width on pair units (see gksl_batch_group_stats).  The environment
+ * variable GKSL_BATCH_TILE=0 forces the 16-byte-gather path, 1..4 the scalar path on rows with
+ * that many instances per lane, p1..p4 the same on pair units (no timing; the cost is then
+ * reported as 0). */
 gksl_status gksl_batch_info(gksl_batch *b, int group, int *instances_per_lane, double *tuned_us_per_step);
-/* Size of group `group`: rows D, instances, and the stored entries of its value channels summed
- * (QH, Q1, [R | K] and a scanned component), which a stage streams once per instance chunk.
- * Any pointer may be NULL. */
+/* Size and path of group `group`: rows D, instances, the stored entries of its value channels
+ * summed (QH, Q1, [R | K] and a scanned component), which the row paths stream once per stage and
+ * instance chunk, the entries of its pair units (rows S^(j,k) and J^(j,k) of one pair share one
+ * merged column list; the D rows stand alone), which the pair path streams instead, and the FP32
+ * path in use: 0 the 16-byte gathers on rows, 1 scalar gathers on rows, 2 scalar gathers on pair
+ * units.  Any pointer may be NULL. */
 gksl_status gksl_batch_group_stats(gksl_batch *b, int group, long long *rows, int *instances,
-                                   long long *channel_entries);
+                                   long long *channel_entries, long long *pair_entries, int *path);
 
 /* ------------------------------------------------------------------ allocation-free propagation */
 

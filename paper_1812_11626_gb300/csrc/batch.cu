@@ -36,6 +36,14 @@ constexpr int kBatchGraphSteps = 32;
 constexpr int kMaxCh = 4;   // QH, Q1, [R | K], and optionally one scanned Hamiltonian component
 
 struct GroupDev {
+    // pair units (FP32 path): unit u < P2 holds the rows u and P2 + u (the S and J generators of
+    // one pair, which couple to nearly the same columns), units u >= P2 the D rows one each; per
+    // unit the union of its rows' columns over all channels, with both rows' channel values
+    const int *pptr;
+    const int *pcol;
+    const float4 *pval;   // 2 per entry: row a {QH, Q1, R|K, scan}, row b (0 for a D unit)
+    long long P2, nunits;
+    int pairs;            // FP32 steps use the pair units
     const int *ptr[kMaxCh];
     const int *col[kMaxCh];
     const float *vf[kMaxCh];
@@ -224,7 +232,83 @@ __device__ inline void row_vec4(const GroupDev &G, long long r, int ch, int lane
     }
 }
 
-template <int STAGE, bool F64>
+// Unit u of the pair form for the instances b0 + 32 k, k < ipl, of this lane: every entry's
+// column is gathered once and serves both rows of the unit (scalar 4-byte gathers, coalesced
+// across lanes), then the two rows' stage updates.
+template <int STAGE>
+__device__ inline void unit_pair(const GroupDev &G, long long u, int ch, int lane, long long step) {
+    const int B = G.B;
+    const long long Bs = G.Bs;
+    const float *X = STAGE == 1 ? G.V32 : (STAGE == 3 ? G.Y32[1] : G.Y32[0]);
+    const bool scan = G.nch > 3;
+    float acc[2][kMaxCh][kMaxIpl];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < kMaxCh; ++c)
+#pragma unroll
+            for (int k = 0; k < kMaxIpl; ++k) acc[q][c][k] = 0.f;
+    const int b0 = ch * 32 * G.ipl + lane;
+    const int e1 = G.pptr[u + 1];
+    constexpr int U = 2;
+    int e = G.pptr[u];
+    for (; e + U <= e1; e += U) {
+        int col[U];
+        float x[U][kMaxIpl];
+#pragma unroll
+        for (int v = 0; v < U; ++v) col[v] = G.pcol[e + v];
+#pragma unroll
+        for (int v = 0; v < U; ++v)
+#pragma unroll
+            for (int k = 0; k < kMaxIpl; ++k) {
+                const int b = b0 + 32 * k;
+                x[v][k] = (k < G.ipl && b < B) ? __ldg(X + (long long)col[v] * Bs + b) : 0.f;
+            }
+#pragma unroll
+        for (int v = 0; v < U; ++v) {
+            const float4 wa = G.pval[2 * (e + v)], wb = G.pval[2 * (e + v) + 1];
+#pragma unroll
+            for (int k = 0; k < kMaxIpl; ++k) {
+                acc[0][0][k] += wa.x * x[v][k]; acc[0][1][k] += wa.y * x[v][k]; acc[0][2][k] += wa.z * x[v][k];
+                acc[1][0][k] += wb.x * x[v][k]; acc[1][1][k] += wb.y * x[v][k]; acc[1][2][k] += wb.z * x[v][k];
+                if (scan) { acc[0][3][k] += wa.w * x[v][k]; acc[1][3][k] += wb.w * x[v][k]; }
+            }
+        }
+    }
+    for (; e < e1; ++e) {
+        const int col = G.pcol[e];
+        const float4 wa = G.pval[2 * e], wb = G.pval[2 * e + 1];
+#pragma unroll
+        for (int k = 0; k < kMaxIpl; ++k) {
+            const int b = b0 + 32 * k;
+            const float x = (k < G.ipl && b < B) ? __ldg(X + (long long)col * Bs + b) : 0.f;
+            acc[0][0][k] += wa.x * x; acc[0][1][k] += wa.y * x; acc[0][2][k] += wa.z * x;
+            acc[1][0][k] += wb.x * x; acc[1][1][k] += wb.y * x; acc[1][2][k] += wb.z * x;
+            if (scan) { acc[0][3][k] += wa.w * x; acc[1][3][k] += wb.w * x; }
+        }
+    }
+    const int slot = STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1);
+    const float sn = G.sin_tab_f[3 * step + slot];
+    const long long ra = u < G.P2 ? u : G.P2 + u;   // D units: row 2 P2 + (u - P2)
+    const int nrows = u < G.P2 ? 2 : 1;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (q >= nrows) break;
+        const long long r = q == 0 ? ra : u + G.P2;
+#pragma unroll
+        for (int k = 0; k < kMaxIpl; ++k) {
+            const int b = b0 + 32 * k;
+            if (k >= G.ipl || b >= B) continue;
+            float kf = acc[q][0][k] + (G.Af[b] * sn) * acc[q][1][k] + G.gf[b] * acc[q][2][k];
+            if (scan) kf += G.Sf[b] * acc[q][3][k];
+            stage_update<STAGE, false>(G, r * Bs + b, 0.0, kf);
+        }
+    }
+}
+
+// PAIRS: the instance with the pair path, launched (FP32 steps) when some group uses it; its
+// accumulators for two rows take more registers, so the row-only instance stays separate
+template <int STAGE, bool F64, bool PAIRS>
 __global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
     const long long step = *a.base + a.local;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -234,8 +318,15 @@ __global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
         const GroupDev &G = a.gr[gi];
         if (step >= G.nsteps) continue;
         long long tl = t - G.tile_begin;
-        long long r = (tl / G.nchunks) * kRowsPerTile + warp;
         int ch = (int)(tl % G.nchunks);
+        if constexpr (PAIRS && !F64) {
+            if (G.pairs) {
+                const long long u = (tl / G.nchunks) * kRowsPerTile + warp;
+                if (u < G.nunits) unit_pair<STAGE>(G, u, ch, lane, step);
+                continue;
+            }
+        }
+        long long r = (tl / G.nchunks) * kRowsPerTile + warp;
         if (r >= G.D) continue;
         if (!F64 && G.vec4) row_vec4<STAGE>(G, r, ch, lane, step);
         else row_scalar<STAGE, F64>(G, r, ch, lane, step);
@@ -307,6 +398,10 @@ struct Group {
     double h = 0.0;
     double t = 0.0;   // time of the group's states
     double tuned_us = 0.0;
+    DBuf<int> pptr, pcol;               // pair units of the FP32 path (see GroupDev)
+    DBuf<float4> pval;
+    long long P2 = 0, nunits = 0, pnnz = 0;
+    bool pairs = false;
     DBuf<double> Vprev;                 // state one period earlier (gksl_batch_asymptotic)
     DBuf<unsigned long long> resid;     // per-instance period-map residual, as double bit patterns
 };
@@ -342,6 +437,87 @@ __global__ void k_f2(const double *__restrict__ v, float *__restrict__ o, long l
     if (i < n) o[i] = (float)v[i];
 }
 
+// Pair units of a group: unit u < P2 merges the sorted column lists of rows u and P2 + u over
+// every channel, unit u >= P2 those of row P2 + u; pass 1 counts a unit's distinct columns, pass 2
+// writes them with both rows' FP32 channel values (0 where a row or channel has no entry).
+struct ChanCsr {
+    const int *ptr[kMaxCh];
+    const int *col[kMaxCh];
+    const float *val[kMaxCh];
+    int nch;
+};
+
+template <bool FILL>
+__global__ void k_pair_units(ChanCsr m, long long P2, long long nunits, long long *__restrict__ cnt,
+                             const int *__restrict__ pptr, int *__restrict__ pcol, float4 *__restrict__ pval) {
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nunits) return;
+    const int nr = u < P2 ? 2 : 1;
+    const long long row[2] = {u < P2 ? u : P2 + u, u + P2};
+    int e[2][kMaxCh], end[2][kMaxCh];
+    for (int q = 0; q < 2; ++q)
+        for (int c = 0; c < kMaxCh; ++c) {
+            const bool on = q < nr && c < m.nch;
+            e[q][c] = on ? m.ptr[c][row[q]] : 0;
+            end[q][c] = on ? m.ptr[c][row[q] + 1] : 0;
+        }
+    long long n = 0, o = FILL ? pptr[u] : 0;
+    for (;;) {
+        int cmin = 0x7fffffff;
+        for (int q = 0; q < 2; ++q)
+            for (int c = 0; c < kMaxCh; ++c)
+                if (e[q][c] < end[q][c] && m.col[c][e[q][c]] < cmin) cmin = m.col[c][e[q][c]];
+        if (cmin == 0x7fffffff) break;
+        float v[2][kMaxCh] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        for (int q = 0; q < 2; ++q)
+            for (int c = 0; c < kMaxCh; ++c)
+                if (e[q][c] < end[q][c] && m.col[c][e[q][c]] == cmin) {
+                    if (FILL) v[q][c] = m.val[c][e[q][c]];
+                    ++e[q][c];
+                }
+        if (FILL) {
+            pcol[o] = cmin;
+            pval[2 * o] = make_float4(v[0][0], v[0][1], v[0][2], v[0][3]);
+            pval[2 * o + 1] = make_float4(v[1][0], v[1][1], v[1][2], v[1][3]);
+            ++o;
+        }
+        ++n;
+    }
+    if (!FILL) cnt[u] = n;
+}
+
+__global__ void k_ll_to_i32(const long long *__restrict__ in, long long n, int *__restrict__ out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int)in[i];
+}
+
+void build_pairs(Group &G, cudaStream_t s) {
+    ChanCsr m{};
+    m.nch = G.nch;
+    for (int c = 0; c < G.nch; ++c) {
+        m.ptr[c] = G.m[c].rowptr.p;
+        m.col[c] = G.m[c].col.p;
+        m.val[c] = G.mf[c].p;
+    }
+    G.P2 = G.ctx->P2;
+    G.nunits = G.D - G.P2;
+    const long long nu = G.nunits;
+    DBuf<long long> cnt((size_t)nu), off((size_t)nu + 1);
+    k_pair_units<false><<<grid_for(nu, 256), 256, 0, s>>>(m, G.P2, nu, cnt.p, nullptr, nullptr, nullptr);
+    GK_LAUNCH_CHECK();
+    const long long nnz = scan_ll(cnt.p, off.p, nu, true, true, s);
+    GK_REQUIRE(nnz < (1LL << 30), GKSL_ERR_ARG, "batched group too large for the pair form");
+    G.pptr.alloc((size_t)nu + 1);
+    G.pcol.alloc((size_t)std::max(1LL, nnz));
+    G.pval.alloc((size_t)std::max(1LL, 2 * nnz));
+    k_ll_to_i32<<<grid_for(nu + 1, 256), 256, 0, s>>>(off.p, nu + 1, G.pptr.p);
+    GK_LAUNCH_CHECK();
+    k_pair_units<true><<<grid_for(nu, 256), 256, 0, s>>>(m, G.P2, nu, nullptr, G.pptr.p, G.pcol.p, G.pval.p);
+    GK_LAUNCH_CHECK();
+    G.pnnz = nnz;
+    GK_CUDA(cudaStreamSynchronize(s));
+}
+
 BatchArgs make_args(gksl_batch *b, bool f64, long long local) {
     BatchArgs a{};
     a.ng = (int)b->groups.size();
@@ -356,6 +532,12 @@ BatchArgs make_args(gksl_batch *b, bool f64, long long local) {
             d.vd[c] = G.m[c].val.p;
         }
         d.nch = G.nch;
+        d.pptr = G.pptr.p;
+        d.pcol = G.pcol.p;
+        d.pval = G.pval.p;
+        d.P2 = G.P2;
+        d.nunits = G.nunits;
+        d.pairs = (!f64 && G.pairs) ? 1 : 0;
         d.S = G.S.p;
         d.Sf = G.Sf.p;
         d.D = G.D;
@@ -386,7 +568,8 @@ BatchArgs make_args(gksl_batch *b, bool f64, long long local) {
         d.Y64[1] = G.Y64b.p;
         d.ACC64 = G.ACC64.p;
         d.tile_begin = tb;
-        d.ntiles = ((G.D + kRowsPerTile - 1) / kRowsPerTile) * d.nchunks;
+        const long long units = d.pairs ? G.nunits : G.D;   // warps' work items: pair units or rows
+        d.ntiles = ((units + kRowsPerTile - 1) / kRowsPerTile) * d.nchunks;
         tb += d.ntiles;
     }
     a.ntiles = tb;
@@ -408,16 +591,23 @@ void launch_batch_step(gksl_batch *b, bool f64, long long local) {
     BatchArgs a = make_args(b, f64, local);
     unsigned grid = batch_grid(a.ntiles);
     cudaStream_t s = b->stream;
+    bool pairs = false;
+    for (int i = 0; i < a.ng; ++i) pairs = pairs || a.gr[i].pairs;
     if (f64) {
-        k_batch_stage<1, true><<<grid, kBThreads, 0, s>>>(a);
-        k_batch_stage<2, true><<<grid, kBThreads, 0, s>>>(a);
-        k_batch_stage<3, true><<<grid, kBThreads, 0, s>>>(a);
-        k_batch_stage<4, true><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<1, true, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<2, true, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<3, true, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<4, true, false><<<grid, kBThreads, 0, s>>>(a);
+    } else if (pairs) {
+        k_batch_stage<1, false, true><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<2, false, true><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<3, false, true><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<4, false, true><<<grid, kBThreads, 0, s>>>(a);
     } else {
-        k_batch_stage<1, false><<<grid, kBThreads, 0, s>>>(a);
-        k_batch_stage<2, false><<<grid, kBThreads, 0, s>>>(a);
-        k_batch_stage<3, false><<<grid, kBThreads, 0, s>>>(a);
-        k_batch_stage<4, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<1, false, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<2, false, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<3, false, false><<<grid, kBThreads, 0, s>>>(a);
+        k_batch_stage<4, false, false><<<grid, kBThreads, 0, s>>>(a);
     }
     GK_LAUNCH_CHECK();
 }
@@ -476,19 +666,24 @@ void reset_batch(gksl_batch *b) {
 void autotune(gksl_batch *b) {
     std::vector<Group *> all;
     for (auto &G : b->groups) all.push_back(&G);
-    // GKSL_BATCH_TILE=0 forces the 16-byte-gather path, 1..4 the scalar path with that many
-    // instances per lane (for tests of each path; normally chosen by timing)
+    // GKSL_BATCH_TILE=0 forces the 16-byte-gather path, 1..4 the scalar row path with that many
+    // instances per lane, p1..p4 the pair path (for tests of each path; normally chosen by timing)
     const char *env = getenv("GKSL_BATCH_TILE");
-    if (env && env[0] >= '0' && env[0] <= '0' + kMaxIpl && env[1] == 0) {
-        const int f = env[0] - '0';
-        for (auto *G : all) {
-            G->vec4 = f == 0;
-            G->ipl = f == 0 ? 1 : f;
-            G->tuned_us = 0.0;
+    if (env) {
+        const bool pr = env[0] == 'p';
+        const char *d = pr ? env + 1 : env;
+        if (d[0] >= (pr ? '1' : '0') && d[0] <= '0' + kMaxIpl && d[1] == 0) {
+            const int f = d[0] - '0';
+            for (auto *G : all) {
+                G->pairs = pr;
+                G->vec4 = !pr && f == 0;
+                G->ipl = f == 0 ? 1 : f;
+                G->tuned_us = 0.0;
+            }
+            clear_batch_graphs(b);
+            b->tuned = true;
+            return;
         }
-        clear_batch_graphs(b);
-        b->tuned = true;
-        return;
     }
     cudaEvent_t e0, e1;
     GK_CUDA(cudaEventCreate(&e0));
@@ -507,10 +702,14 @@ void autotune(gksl_batch *b) {
         GK_LAUNCH_CHECK();
         double best = 1e300;
         int best_ipl = 1;
-        bool best_vec4 = false;
-        // candidates: the 16-byte gather path (ipl = 0 below), then 1..4 scalar instances per lane
-        for (int ipl = 0; ipl <= kMaxIpl; ++ipl) {
-            if (ipl > 0 && 32 * (ipl - 1) >= G->B) break;   // wider chunks than the batch add nothing
+        bool best_vec4 = false, best_pairs = false;
+        // candidates: the 16-byte gather path (ipl = 0 below), 1..4 scalar instances per lane on
+        // rows, then the same on pair units
+        for (int cand = 0; cand <= 2 * kMaxIpl; ++cand) {
+            const bool pr = cand > kMaxIpl;
+            const int ipl = pr ? cand - kMaxIpl : cand;
+            if (ipl > 0 && 32 * (ipl - 1) >= G->B) continue;   // wider chunks than the batch add nothing
+            G->pairs = pr;
             G->vec4 = (ipl == 0);
             G->ipl = ipl == 0 ? 1 : ipl;
             G->h = 1e-6;   // tiny step: the trial leaves the state essentially unchanged
@@ -522,10 +721,11 @@ void autotune(gksl_batch *b) {
             GK_CUDA(cudaEventSynchronize(e1));
             float ms = 0;
             GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; best_ipl = G->ipl; best_vec4 = G->vec4; }
+            if (ms < best) { best = ms; best_ipl = G->ipl; best_vec4 = G->vec4; best_pairs = G->pairs; }
         }
         G->ipl = best_ipl;
         G->vec4 = best_vec4;
+        G->pairs = best_pairs;
         G->tuned_us = best * 1000.0 / 8.0;
         for (size_t i = 0; i < all.size(); ++i) all[i]->nsteps = saved[i];
     }
@@ -616,6 +816,7 @@ extern "C" gksl_status gksl_batch_create(int n_groups, gksl_ctx *const *groups, 
                 }
             }
             GK_CUDA(cudaStreamSynchronize(s));
+            build_pairs(G, s);
             G.A.alloc((size_t)G.B);
             G.g.alloc((size_t)G.B);
             G.Af.alloc((size_t)G.B);
@@ -866,6 +1067,7 @@ extern "C" gksl_status gksl_batch_set_scan(gksl_batch *b, int component, const d
             GK_CUDA(cudaMemcpy(G.S.p, s.data(), sizeof(double) * G.B, cudaMemcpyHostToDevice));
             GK_CUDA(cudaMemcpy(G.Sf.p, sf.data(), sizeof(float) * G.B, cudaMemcpyHostToDevice));
             G.nch = 4;
+            build_pairs(G, b->stream);
         }
         GK_CUDA(cudaStreamSynchronize(b->stream));
         clear_batch_graphs(b);
@@ -874,12 +1076,14 @@ extern "C" gksl_status gksl_batch_set_scan(gksl_batch *b, int component, const d
 }
 
 extern "C" gksl_status gksl_batch_group_stats(gksl_batch *b, int group, long long *rows, int *instances,
-                                              long long *channel_entries) {
+                                              long long *channel_entries, long long *pair_entries, int *path) {
     return bguarded(b, [&] {
         GK_REQUIRE(group >= 0 && group < (int)b->groups.size(), GKSL_ERR_ARG, "bad group");
         const Group &G = b->groups[group];
         if (rows) *rows = G.D;
         if (instances) *instances = G.B;
+        if (pair_entries) *pair_entries = G.pnnz;
+        if (path) *path = G.pairs ? 2 : (G.vec4 ? 0 : 1);
         if (channel_entries) {
             long long n = 0;
             for (int c = 0; c < G.nch; ++c) n += G.m[c].nnz;

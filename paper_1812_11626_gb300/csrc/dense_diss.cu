@@ -38,17 +38,19 @@ __device__ inline double2 cscale(double2 a, double s) { return make_double2(a.x 
 // (D^l)_cc for c = 0..l.
 struct Gen {
     int kind, x, y;   // kind 0: S, 1: J, 2: D^x
+    double cl;        // c_x = 1/sqrt(x(x+1)) of a D generator, computed once
     __device__ Gen(const Basis &B, long long s) {
         El e = B.decode(s);
         kind = e.kind;
         x = e.a;
         y = e.b;
+        cl = kind == 2 ? gk::cl(x) : 0.0;
     }
     __device__ int count() const { return kind == 2 ? x + 1 : 2; }
     __device__ void entry(int t, int &r, int &c, double2 &v) const {
-        if (kind == 2) {
+        if (kind == 2) {   // (D^x)_tt = c_x for t < x, -x c_x for t = x
             r = c = t;
-            v = make_double2(dl_diag(x, t), 0.0);
+            v = make_double2(t < x ? cl : -(double)x * cl, 0.0);
         } else if (t == 0) {
             r = x; c = y;
             v = kind == 0 ? make_double2(GK_RSQRT2, 0.0) : make_double2(0.0, -GK_RSQRT2);

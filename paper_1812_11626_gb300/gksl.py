@@ -91,7 +91,8 @@ _SIGS = {
     "gksl_batch_get_state": (_S, [_P, _I, _P]),
     "gksl_batch_info": (_S, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "gksl_batch_set_scan": (_S, [_P, _I, _P]),
-    "gksl_batch_group_stats": (_S, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_I), ctypes.POINTER(_L)]),
+    "gksl_batch_group_stats": (_S, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_I), ctypes.POINTER(_L),
+                                    ctypes.POINTER(_L), ctypes.POINTER(_I)]),
     "gksl_batch_asymptotic": (_S, [_P, _P, _L, _L, _D, _L, _P, ctypes.POINTER(_L)]),
     "gksl_get_info": (_S, [_P, ctypes.POINTER(gksl_info)]),
     "gksl_measure_rates": (_S, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -323,11 +324,12 @@ def gksl_batch_asymptotic(b, steps_per_period, transient, max_periods, tol, corr
 
 
 def gksl_batch_group_stats(b, group):
-    """(rows D, instances, stored entries summed over the value channels) of one group."""
-    rows, inst, ent = _L(), _I(), _L()
-    _check(_lib.gksl_batch_group_stats(b, int(group), ctypes.byref(rows), ctypes.byref(inst), ctypes.byref(ent)),
-           batch=b)
-    return rows.value, inst.value, ent.value
+    """(rows D, instances, channel entries, pair-unit entries, FP32 path: 0 16-byte rows, 1 scalar
+    rows, 2 pair units) of one group."""
+    rows, inst, ent, pent, path = _L(), _I(), _L(), _L(), _I()
+    _check(_lib.gksl_batch_group_stats(b, int(group), ctypes.byref(rows), ctypes.byref(inst), ctypes.byref(ent),
+                                       ctypes.byref(pent), ctypes.byref(path)), batch=b)
+    return rows.value, inst.value, ent.value, pent.value, path.value
 
 
 def gksl_batch_info(b, group):

@@ -16,11 +16,12 @@ def G():
     return gksl
 
 
-@pytest.mark.parametrize("tile", ["auto", "0", "1", "3"])
+@pytest.mark.parametrize("tile", ["auto", "0", "1", "3", "p1", "p3"])
 def test_batch_mixed_n_vs_oracle(G, tile, monkeypatch):
-    """Mixed N in one batch, every instance path: the autotuner's choice, the 16-byte-gather path on
-    the union pattern (tile 0, shared-memory staging) and the scalar paths with 1 and 3 instances
-    per lane, each against per-instance oracle runs."""
+    """Mixed N in one batch, every instance path: the autotuner's choice, the 16-byte-gather path
+    (tile 0), the scalar paths on rows with 1 and 3 instances per lane, and the same on pair units
+    (p1, p3: the S and J rows of a pair read one merged column list), each against per-instance
+    oracle runs."""
     if tile != "auto":
         monkeypatch.setenv("GKSL_BATCH_TILE", tile)
     sizes = [(5, 3), (9, 40), (12, 70)]   # (N, instances): chunk widths 1..3 warps of lanes
@@ -52,7 +53,9 @@ def test_batch_mixed_n_vs_oracle(G, tile, monkeypatch):
             if tile == "auto":
                 assert 1 <= ipl <= 4 and us > 0
             else:   # forced: no timing, the forced width (4 for the 16-byte path)
-                assert ipl == (4 if tile == "0" else int(tile)) and us == 0
+                assert ipl == (4 if tile == "0" else int(tile.lstrip("p"))) and us == 0
+                path = G.gksl_batch_group_stats(b, gi)[4]
+                assert path == (2 if tile.startswith("p") else (0 if tile == "0" else 1))
     finally:
         G.gksl_batch_destroy(b)
         for c in ctxs:
@@ -88,12 +91,12 @@ def test_batch_256_seeded_instances_sampled(G, record):
             G.gksl_destroy(c)
 
 
-@pytest.mark.parametrize("tile", ["auto", "0", "2"])
+@pytest.mark.parametrize("tile", ["auto", "0", "2", "p2"])
 def test_bifurcation_scan_vs_oracle(G, tile, monkeypatch):
     """U-scan of the dimer as one batch (a per-instance interaction weight): populations
     diag rho after 2 periods for 8 values of U against single-instance oracle runs, and the
     populations are a probability distribution; with the scanned component as the fourth value
-    channel of the union pattern (tile 0) and of the scalar path (tile 2)."""
+    channel of the 16-byte path (tile 0), the scalar row path (2) and the pair path (p2)."""
     if tile != "auto":
         monkeypatch.setenv("GKSL_BATCH_TILE", tile)
     N = 12
