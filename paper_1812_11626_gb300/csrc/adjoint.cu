@@ -24,6 +24,7 @@
 // without room for every checkpoint); memory is periods * S/q state checkpoints (periods + S/q
 // without room) plus 4 q stage inputs.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -57,6 +58,7 @@ struct AdjArgs {
     long long n_long;
     int nb_long;
     long long D;
+    int split;      // reverse stages in the channel-split form (k_adjoint_cs)
 };
 
 // (C x)_r over the ELL slots of row r; the slot loads go out four at a time before their gathers
@@ -230,6 +232,97 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
     }
 }
 
+// Channel-split form of k_adjoint for small systems (4 channels): the first nb_long blocks treat
+// the long rows as k_adjoint does; elsewhere four consecutive lanes share a row, lane c applying
+// channel c (u_c = (C_c x)_r) and keeping its gradient partial u_c . Y_r in its own slot, so a
+// row waits only for its longest channel and a block of 4 bt threads covers as many rows as
+// k_adjoint's block of bt.  The weighted sum over the channels takes two shuffles; the first lane
+// of the four adds the K partials and writes the stage's update.  Same block count and slots as
+// k_adjoint, same per-row arithmetic except the order of the four-term channel sum.
+template <int STAGE, typename VT>
+__global__ void __launch_bounds__(kThreads) k_adjoint_cs(AdjArgs<VT> a, const VT *__restrict__ x,
+                                                        const VT *__restrict__ Y, const double *lam, double *lacc,
+                                                        VT *__restrict__ kb_out, const double *__restrict__ w,
+                                                        double *lam_out, double *__restrict__ part) {
+    constexpr int NC = 4, NSLOT = 2 * NC;
+    const long long step = *a.base + a.local;
+    const double th = a.theta[3 * step + (STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1))];
+    const double alpha = STAGE == 4 ? a.h6 : 1.0;
+    double beta = 0.0;
+    if (STAGE == 1) {
+        const long long m = step - a.first;
+        beta = (m >= 0 && m < a.S) ? (m == 0 ? a.w_edge : a.w_mid) : 0.0;
+    }
+    double chw[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) chw[c] = c == a.q1ch ? a.E + a.A * th : (c < a.nch ? a.chw[c] : 0.0);
+    double g[NSLOT];
+#pragma unroll
+    for (int k = 0; k < NSLOT; ++k) g[k] = 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nthr = blockDim.x, nwarp = nthr >> 5;
+    if ((int)blockIdx.x < a.nb_long) {
+        double u[NC];
+        for (long long i = (long long)blockIdx.x * nwarp + warp; i < a.n_long; i += (long long)a.nb_long * nwarp) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) u[c] = c < a.nch ? tail_row<VT>(a.ch[c], i, lane, x) : 0.0;
+            if (lane == 0) {
+                const long long r = a.long_rows[i];
+                const double yr = (double)Y[r];
+                double ysum = 0.0;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    ysum += chw[c] * u[c];
+                    g[c] += u[c] * yr;
+                }
+                const double xr = (double)x[r];
+#pragma unroll
+                for (int q = 0; q < NC; ++q)
+                    if (q < a.nkp) g[NC + q] += xr * a.kp[q][r];
+                adj_epilogue<STAGE, VT>(a, r, alpha * ysum, lam, lacc, kb_out, w, lam_out, beta);
+            }
+        }
+    } else {
+        const int c = threadIdx.x & 3;
+        const long long per = nthr >> 2;   // rows per block pass
+        const long long stride = (long long)(gridDim.x - a.nb_long) * per;
+        // every lane runs the same number of passes (the shuffles need all four lanes of a row)
+        for (long long r0 = (long long)(blockIdx.x - a.nb_long) * per; r0 < a.D; r0 += stride) {
+            const long long r = r0 + (threadIdx.x >> 2);
+            const bool live = r < a.D && __ldcs(a.ch[0].ell_col + (r < a.D ? r : 0)) >= 0;
+            double u = 0.0;
+            if (live && c < a.nch) u = ell_row<VT>(a.ch[c], r, x);
+            double ys = chw[c] * u;
+            ys += __shfl_xor_sync(0xffffffffu, ys, 1);
+            ys += __shfl_xor_sync(0xffffffffu, ys, 2);
+            if (!live) continue;
+            const double yr = (double)Y[r];
+#pragma unroll
+            for (int k = 0; k < NC; ++k)
+                if (k == c) g[k] += u * yr;
+            if (c == 0) {
+                const double xr = (double)x[r];
+#pragma unroll
+                for (int q = 0; q < NC; ++q)
+                    if (q < a.nkp) g[NC + q] += xr * a.kp[q][r];
+                adj_epilogue<STAGE, VT>(a, r, alpha * ys, lam, lacc, kb_out, w, lam_out, beta);
+            }
+        }
+    }
+    __shared__ double red[kWarps][NSLOT];
+    warp_sum8(g, lane);
+    if ((lane & 3) == 0) red[warp][4 * (lane >> 4 & 1) + 2 * (lane >> 3 & 1) + (lane >> 2 & 1)] = g[0];
+    __syncthreads();
+    if (threadIdx.x < NSLOT) {
+        const int k = threadIdx.x;
+        double sum = 0.0;
+        for (int ww = 0; ww < nwarp; ++ww) sum += red[ww][k];
+        double f = alpha;
+        if (k == a.q1ch) f *= th;
+        part[(long long)blockIdx.x * NSLOT + k] += f * sum;
+    }
+}
+
 // blocks of one reverse stage: up to one per SM for the long rows (a warp each), then the ELL
 // rows (a thread each), both walked with a grid stride; at most 1024 threads per SM in all (the
 // register budget of the 4-channel kernel), so the whole grid is resident at once.  Blocks are
@@ -326,6 +419,16 @@ template <typename VT, int NC>
 void rev_stages_t(const AdjArgs<VT> &a, unsigned grid, int bt, cudaStream_t s, const VT *lam_in, const VT *Y1, const VT *Y2,
                   const VT *Y3, const VT *Y4, VT *ka, VT *kb, double *lam, double *lacc, const double *w,
                   double *part) {
+    if constexpr (NC == 4) {
+        if (a.split) {   // channel-split form: the same blocks with four lanes per row
+            const int bs = 4 * bt;
+            k_adjoint_cs<4, VT><<<grid, bs, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
+            k_adjoint_cs<3, VT><<<grid, bs, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
+            k_adjoint_cs<2, VT><<<grid, bs, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
+            k_adjoint_cs<1, VT><<<grid, bs, 0, s>>>(a, ka, Y1, lam, lacc, nullptr, w, lam, part);
+            return;
+        }
+    }
     k_adjoint<4, VT, NC><<<grid, bt, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
     k_adjoint<3, VT, NC><<<grid, bt, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
     k_adjoint<2, VT, NC><<<grid, bt, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
@@ -417,6 +520,15 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
     GK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const AdjGrid ag = adj_grid(a64.n_long, D, sms);
     a64.nb_long = a32.nb_long = ag.nb_long;
+    // channel-split reverse stages where the rows are few enough that blocks were shrunk to 64
+    // threads (four lanes per row then fill 256-thread blocks); GKSL_ADJ_SPLIT=0/1 forces it off/on
+    // where it applies (at most 4 channels, 64-thread blocks)
+    {
+        const bool can = c->adj_n <= 4 && ag.threads * 4 <= kThreads;
+        const char *env = getenv("GKSL_ADJ_SPLIT");
+        const bool want = env ? env[0] == '1' : true;
+        a64.split = a32.split = (can && want) ? 1 : 0;
+    }
     const unsigned grid = ag.total;
     // channels compiled into the kernel: 4 (one dissipator, up to two H0 components), or all
     const int NC = c->adj_n <= 4 ? 4 : kMaxCh;
