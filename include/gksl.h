@@ -223,10 +223,7 @@ gksl_status gksl_rho(gksl_ctx *ctx, const double *v, double *re, double *im);
  * the discrete adjoint of the RK4 map (per-period checkpoints, recomputation in between).
  * grad receives n_grad doubles in the order [d/dA, d/dgamma_0 .. d/dgamma_{P-1},
  * d/dtheta_0 .. d/dtheta_{K-1}] over the set channels and components in index order.
- * Requires gksl_assemble with GKSL_ASM_TRANSPOSE.  The state is left unchanged.  For small
- * systems (at most 4 parameter channels, rows too few for blocks of more than 64 threads) the
- * reverse stages run in a channel-split form, four lanes per row; the environment variable
- * GKSL_ADJ_SPLIT=0 turns that off. */
+ * Requires gksl_assemble with GKSL_ASM_TRANSPOSE.  The state is left unchanged. */
 gksl_status gksl_adjoint_timeavg(gksl_ctx *ctx, const double *o_diag, long long steps_per_period,
                                  long long period_index, int precision, double *loss, double *grad, int n_grad);
 

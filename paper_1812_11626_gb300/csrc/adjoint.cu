@@ -16,15 +16,17 @@
 //
 // Schedule: checkpoints every q steps (q ~ sqrt(S/4)) from one forward pass when they fit in
 // memory, else period checkpoints and, period by period in reverse, a forward pass that sets
-// the checkpoints of the period's segments; then segment by segment in reverse one CUDA graph
+// the checkpoints of the period's segments; then segment by segment in reverse a CUDA graph
 // that re-runs the segment's q steps forward, keeping every stage input Y1..Y4 of each step,
-// and then sweeps the same steps backwards.  Every per-step scalar (the drive at the stage
+// and one that sweeps the same steps backwards on a second stream.  With two stage-input
+// buffers the forward graph of the next segment runs while the current one is swept backwards
+// (the small systems' kernels leave most of the GPU idle); events order each buffer's writer
+// after its previous reader.  Every per-step scalar (the drive at the stage
 // times, the loss weight of the step) is read from device tables indexed by the step, so one
 // graph per segment length serves every segment.  Each state is computed twice (three times
 // without room for every checkpoint); memory is periods * S/q state checkpoints (periods + S/q
 // without room) plus 4 q stage inputs.
 #include <algorithm>
-#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -58,7 +60,6 @@ struct AdjArgs {
     long long n_long;
     int nb_long;
     long long D;
-    int split;      // reverse stages in the channel-split form (k_adjoint_cs)
 };
 
 // (C x)_r over the ELL slots of row r; the slot loads go out four at a time before their gathers
@@ -232,97 +233,6 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
     }
 }
 
-// Channel-split form of k_adjoint for small systems (4 channels): the first nb_long blocks treat
-// the long rows as k_adjoint does; elsewhere four consecutive lanes share a row, lane c applying
-// channel c (u_c = (C_c x)_r) and keeping its gradient partial u_c . Y_r in its own slot, so a
-// row waits only for its longest channel and a block of 4 bt threads covers as many rows as
-// k_adjoint's block of bt.  The weighted sum over the channels takes two shuffles; the first lane
-// of the four adds the K partials and writes the stage's update.  Same block count and slots as
-// k_adjoint, same per-row arithmetic except the order of the four-term channel sum.
-template <int STAGE, typename VT>
-__global__ void __launch_bounds__(kThreads) k_adjoint_cs(AdjArgs<VT> a, const VT *__restrict__ x,
-                                                        const VT *__restrict__ Y, const double *lam, double *lacc,
-                                                        VT *__restrict__ kb_out, const double *__restrict__ w,
-                                                        double *lam_out, double *__restrict__ part) {
-    constexpr int NC = 4, NSLOT = 2 * NC;
-    const long long step = *a.base + a.local;
-    const double th = a.theta[3 * step + (STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1))];
-    const double alpha = STAGE == 4 ? a.h6 : 1.0;
-    double beta = 0.0;
-    if (STAGE == 1) {
-        const long long m = step - a.first;
-        beta = (m >= 0 && m < a.S) ? (m == 0 ? a.w_edge : a.w_mid) : 0.0;
-    }
-    double chw[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) chw[c] = c == a.q1ch ? a.E + a.A * th : (c < a.nch ? a.chw[c] : 0.0);
-    double g[NSLOT];
-#pragma unroll
-    for (int k = 0; k < NSLOT; ++k) g[k] = 0.0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nthr = blockDim.x, nwarp = nthr >> 5;
-    if ((int)blockIdx.x < a.nb_long) {
-        double u[NC];
-        for (long long i = (long long)blockIdx.x * nwarp + warp; i < a.n_long; i += (long long)a.nb_long * nwarp) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) u[c] = c < a.nch ? tail_row<VT>(a.ch[c], i, lane, x) : 0.0;
-            if (lane == 0) {
-                const long long r = a.long_rows[i];
-                const double yr = (double)Y[r];
-                double ysum = 0.0;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    ysum += chw[c] * u[c];
-                    g[c] += u[c] * yr;
-                }
-                const double xr = (double)x[r];
-#pragma unroll
-                for (int q = 0; q < NC; ++q)
-                    if (q < a.nkp) g[NC + q] += xr * a.kp[q][r];
-                adj_epilogue<STAGE, VT>(a, r, alpha * ysum, lam, lacc, kb_out, w, lam_out, beta);
-            }
-        }
-    } else {
-        const int c = threadIdx.x & 3;
-        const long long per = nthr >> 2;   // rows per block pass
-        const long long stride = (long long)(gridDim.x - a.nb_long) * per;
-        // every lane runs the same number of passes (the shuffles need all four lanes of a row)
-        for (long long r0 = (long long)(blockIdx.x - a.nb_long) * per; r0 < a.D; r0 += stride) {
-            const long long r = r0 + (threadIdx.x >> 2);
-            const bool live = r < a.D && __ldcs(a.ch[0].ell_col + (r < a.D ? r : 0)) >= 0;
-            double u = 0.0;
-            if (live && c < a.nch) u = ell_row<VT>(a.ch[c], r, x);
-            double ys = chw[c] * u;
-            ys += __shfl_xor_sync(0xffffffffu, ys, 1);
-            ys += __shfl_xor_sync(0xffffffffu, ys, 2);
-            if (!live) continue;
-            const double yr = (double)Y[r];
-#pragma unroll
-            for (int k = 0; k < NC; ++k)
-                if (k == c) g[k] += u * yr;
-            if (c == 0) {
-                const double xr = (double)x[r];
-#pragma unroll
-                for (int q = 0; q < NC; ++q)
-                    if (q < a.nkp) g[NC + q] += xr * a.kp[q][r];
-                adj_epilogue<STAGE, VT>(a, r, alpha * ys, lam, lacc, kb_out, w, lam_out, beta);
-            }
-        }
-    }
-    __shared__ double red[kWarps][NSLOT];
-    warp_sum8(g, lane);
-    if ((lane & 3) == 0) red[warp][4 * (lane >> 4 & 1) + 2 * (lane >> 3 & 1) + (lane >> 2 & 1)] = g[0];
-    __syncthreads();
-    if (threadIdx.x < NSLOT) {
-        const int k = threadIdx.x;
-        double sum = 0.0;
-        for (int ww = 0; ww < nwarp; ++ww) sum += red[ww][k];
-        double f = alpha;
-        if (k == a.q1ch) f *= th;
-        part[(long long)blockIdx.x * NSLOT + k] += f * sum;
-    }
-}
-
 // blocks of one reverse stage: up to one per SM for the long rows (a warp each), then the ELL
 // rows (a thread each), both walked with a grid stride; at most 1024 threads per SM in all (the
 // register budget of the 4-channel kernel), so the whole grid is resident at once.  Blocks are
@@ -342,6 +252,8 @@ AdjGrid adj_grid(long long n_long, long long D, int sms) {
     long long ne = std::min<long long>((D + bt - 1) / bt, per_sm * sms - nl);
     return AdjGrid{(int)nl, (unsigned)(nl + std::max(1LL, ne)), bt};
 }
+
+__global__ void k_set_step(long long *p, long long v) { *p = v; }
 
 __global__ void k_fill_scaled(double *__restrict__ y, const double *__restrict__ x, double a, long long n) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -419,16 +331,6 @@ template <typename VT, int NC>
 void rev_stages_t(const AdjArgs<VT> &a, unsigned grid, int bt, cudaStream_t s, const VT *lam_in, const VT *Y1, const VT *Y2,
                   const VT *Y3, const VT *Y4, VT *ka, VT *kb, double *lam, double *lacc, const double *w,
                   double *part) {
-    if constexpr (NC == 4) {
-        if (a.split) {   // channel-split form: the same blocks with four lanes per row
-            const int bs = 4 * bt;
-            k_adjoint_cs<4, VT><<<grid, bs, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
-            k_adjoint_cs<3, VT><<<grid, bs, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
-            k_adjoint_cs<2, VT><<<grid, bs, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
-            k_adjoint_cs<1, VT><<<grid, bs, 0, s>>>(a, ka, Y1, lam, lacc, nullptr, w, lam, part);
-            return;
-        }
-    }
     k_adjoint<4, VT, NC><<<grid, bt, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
     k_adjoint<3, VT, NC><<<grid, bt, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
     k_adjoint<2, VT, NC><<<grid, bt, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
@@ -520,15 +422,6 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
     GK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const AdjGrid ag = adj_grid(a64.n_long, D, sms);
     a64.nb_long = a32.nb_long = ag.nb_long;
-    // channel-split reverse stages where the rows are few enough that blocks were shrunk to 64
-    // threads (four lanes per row then fill 256-thread blocks); GKSL_ADJ_SPLIT=0/1 forces it off/on
-    // where it applies (at most 4 channels, 64-thread blocks)
-    {
-        const bool can = c->adj_n <= 4 && ag.threads * 4 <= kThreads;
-        const char *env = getenv("GKSL_ADJ_SPLIT");
-        const bool want = env ? env[0] == '1' : true;
-        a64.split = a32.split = (can && want) ? 1 : 0;
-    }
     const unsigned grid = ag.total;
     // channels compiled into the kernel: 4 (one dissipator, up to two H0 components), or all
     const int NC = c->adj_n <= 4 ? 4 : kMaxCh;
@@ -558,12 +451,25 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
     // carries the constant 1 at index D (it multiplies the K column)
     const size_t esz = f32 ? sizeof(float) : sizeof(double);
     const long long ytot = 4 * q * D1;
-    DBuf<char> ybuf((size_t)ytot * esz), kbA((size_t)D1 * esz), kbB((size_t)D1 * esz);
+    // two stage-input buffers when they fit in a tenth of the free memory: the forward pass of
+    // the next segment (on the context stream) then overlaps the reverse sweep of the current one
+    // (on a second stream, with its own step counter); otherwise one buffer and the two alternate
+    GK_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const int nbuf = (double)(2 * ytot * esz) <= 0.1 * (double)free_b ? 2 : 1;
+    DBuf<char> ybufs[2];
+    for (int b = 0; b < nbuf; ++b) {
+        ybufs[b].alloc((size_t)ytot * esz);
+        k_fill1<<<grid_for(ytot, 256), 256, 0, s>>>(ybufs[b].p, ytot, f32 ? 1 : 0);
+        GK_LAUNCH_CHECK();
+    }
+    DBuf<char> kbA((size_t)D1 * esz), kbB((size_t)D1 * esz);
     DBuf<float> lamf;
     if (f32) lamf.alloc((size_t)D1);
-    k_fill1<<<grid_for(ytot, 256), 256, 0, s>>>(ybuf.p, ytot, f32 ? 1 : 0);
-    GK_LAUNCH_CHECK();
-    auto Yp = [&](int k, long long i) -> void * { return ybuf.p + (size_t)((k * q + i) * D1) * esz; };
+    DBuf<long long> rbase(1);   // step counter of the reverse stream
+    a64.base = a32.base = rbase.p;
+    auto Yp = [&](int b, int k, long long i) -> void * {
+        return ybufs[b].p + (size_t)((k * q + i) * D1) * esz;
+    };
     GK_CUDA(cudaMemcpyAsync(v_save.p, c->v.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, s));
 
     auto load_state = [&](const double *src) {
@@ -574,23 +480,26 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
         GK_CUDA(cudaMemcpyAsync(dst, c->v.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, s));
     };
 
-    // one reverse step (the four adjoint stages) of local step i of a segment
-    auto reverse_step = [&](long long i) {
+    // one reverse step (the four adjoint stages) of local step i of a segment, stage inputs in
+    // buffer b, on stream st
+    auto reverse_step = [&](long long i, int b, cudaStream_t st) {
         if (f32) {
-            to_f32(lam.p, lamf.p, D1, s);
+            to_f32(lam.p, lamf.p, D1, st);
             AdjArgs<float> a = a32;
             a.local = i;
-            const float *Y1 = (const float *)Yp(0, i), *Y2 = (const float *)Yp(1, i), *Y3 = (const float *)Yp(2, i),
-                        *Y4 = (const float *)Yp(3, i);
+            const float *Y1 = (const float *)Yp(b, 0, i), *Y2 = (const float *)Yp(b, 1, i),
+                        *Y3 = (const float *)Yp(b, 2, i), *Y4 = (const float *)Yp(b, 3, i);
             float *ka = (float *)kbA.p, *kb = (float *)kbB.p;
-            rev_stages<float>(a, NC, grid, ag.threads, s, lamf.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p, part.p);
+            rev_stages<float>(a, NC, grid, ag.threads, st, lamf.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p,
+                              part.p);
         } else {
             AdjArgs<double> a = a64;
             a.local = i;
-            const double *Y1 = (const double *)Yp(0, i), *Y2 = (const double *)Yp(1, i),
-                         *Y3 = (const double *)Yp(2, i), *Y4 = (const double *)Yp(3, i);
+            const double *Y1 = (const double *)Yp(b, 0, i), *Y2 = (const double *)Yp(b, 1, i),
+                         *Y3 = (const double *)Yp(b, 2, i), *Y4 = (const double *)Yp(b, 3, i);
             double *ka = (double *)kbA.p, *kb = (double *)kbB.p;
-            rev_stages<double>(a, NC, grid, ag.threads, s, lam.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p, part.p);
+            rev_stages<double>(a, NC, grid, ag.threads, st, lam.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p,
+                               part.p);
         }
         GK_LAUNCH_CHECK();
     };
@@ -598,30 +507,50 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
         k_obs_step<<<1, 256, 0, s>>>(w.p, c0.p, B.P2, c->N, c->v.p, c->step_base.p, local, first, S, obs.p);
         GK_LAUNCH_CHECK();
     };
-    // graph of one segment of len steps from the context state at step *step_base:
-    // mode 0: forward only; mode 1: forward keeping Y1..Y4, then the reverse sweep; mode 2: as 1
-    // with the observable at every grid point (the loss period)
+    // graphs of one segment of len steps.  Forward (context stream, from the context state at step
+    // *step_base): mode 0 steps only, mode 1 keeping Y1..Y4 in buffer b, mode 2 as 1 with the
+    // observable at every grid point (the loss period).  Reverse (mode 3, second stream, from
+    // step *rbase): the reverse sweep over buffer b.
+    cudaStream_t s2 = nullptr;
+    GK_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t st;
+        ~StreamGuard() { if (st) cudaStreamDestroy(st); }
+    } s2guard{s2};
     ExecSet execs;
-    auto segment_graph = [&](long long len, int mode) -> cudaGraphExec_t {
+    auto segment_graph = [&](long long len, int mode, int b) -> cudaGraphExec_t {
         for (auto &e : execs.v)
-            if (e.len == len && e.mode == mode) return e.exec;
-        Capture cap(s);
-        for (long long i = 0; i < len; ++i) {
-            if (mode > 0) {
-                if (f32) GK_CUDA(cudaMemcpyAsync(Yp(0, i), c->v32.p, sizeof(float) * D1, cudaMemcpyDeviceToDevice, s));
-                else GK_CUDA(cudaMemcpyAsync(Yp(0, i), c->v.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, s));
+            if (e.len == len && e.mode == mode + 4 * b) return e.exec;
+        Capture cap(mode == 3 ? s2 : s);
+        if (mode == 3) {
+            for (long long i = len - 1; i >= 0; --i) reverse_step(i, b, s2);
+        } else {
+            for (long long i = 0; i < len; ++i) {
+                if (mode > 0) {
+                    if (f32) GK_CUDA(cudaMemcpyAsync(Yp(b, 0, i), c->v32.p, sizeof(float) * D1, cudaMemcpyDeviceToDevice, s));
+                    else GK_CUDA(cudaMemcpyAsync(Yp(b, 0, i), c->v.p, sizeof(double) * D1, cudaMemcpyDeviceToDevice, s));
+                }
+                if (mode == 2) obs_node(i);
+                if (mode > 0) step_into(c, precision, h, i, Yp(b, 1, i), Yp(b, 2, i), Yp(b, 3, i));
+                else step_into(c, precision, h, i, nullptr, nullptr, nullptr);
             }
-            if (mode == 2) obs_node(i);
-            if (mode > 0) step_into(c, precision, h, i, Yp(1, i), Yp(2, i), Yp(3, i));
-            else step_into(c, precision, h, i, nullptr, nullptr, nullptr);
+            if (mode == 2) obs_node(len);
         }
-        if (mode == 2) obs_node(len);
-        if (mode > 0)
-            for (long long i = len - 1; i >= 0; --i) reverse_step(i);
         cudaGraphExec_t e = cap.finish();
-        execs.v.push_back({len, mode, e});
+        execs.v.push_back({len, mode + 4 * b, e});
         return e;
     };
+    struct EventPair {
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        ~EventPair() {
+            for (auto e : ev)
+                if (e) cudaEventDestroy(e);
+        }
+    } evF, evR;   // forward pass into buffer b done / reverse sweep over buffer b done
+    for (int b = 0; b < 2; ++b) {
+        GK_CUDA(cudaEventCreateWithFlags(&evF.ev[b], cudaEventDisableTiming));
+        GK_CUDA(cudaEventCreateWithFlags(&evR.ev[b], cudaEventDisableTiming));
+    }
 
     // 1. forward pass: the checkpoints of every segment (keep_all) or of every period; the end
     // state of the last period is not needed
@@ -632,7 +561,7 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
                 save_state(seg.p + (p * nseg + j) * D1);
                 if (p + 1 == period && j + 1 == nseg) break;
                 set_step_base(c, p * S + j * q);
-                GK_CUDA(cudaGraphLaunch(segment_graph(std::min(q, S - j * q), 0), s));
+                GK_CUDA(cudaGraphLaunch(segment_graph(std::min(q, S - j * q), 0, 0), s));
             }
     } else {
         for (long long p = 0; p < period; ++p) {
@@ -640,9 +569,15 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
             if (p + 1 < period) advance(c, precision, h, p * S, S);
         }
     }
-    // 2. reverse sweep; lam starts as dL/dv at the last grid point
+    // 2. reverse sweep; lam starts as dL/dv at the last grid point.  Segment k (in reverse order)
+    // runs forward into buffer k % nbuf on the context stream, once the reverse sweep that last
+    // read that buffer has finished, and then backwards on the second stream; the forward pass of
+    // segment k + 1 overlaps the reverse sweep of segment k.
     k_fill_scaled<<<grid_for(D1, 256), 256, 0, s>>>(lam.p, w.p, 0.5 / (double)S, D1);
     GK_LAUNCH_CHECK();
+    GK_CUDA(cudaEventRecord(evF.ev[0], s));
+    GK_CUDA(cudaStreamWaitEvent(s2, evF.ev[0], 0));   // lam, the tables and the buffers are ready
+    long long k = 0;
     for (long long p = period - 1; p >= 0; --p) {
         const int mode = (p == period - 1) ? 2 : 1;
         const double *segp = seg.p + (keep_all ? p * nseg * D1 : 0);
@@ -652,16 +587,25 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
                 save_state(seg.p + j * D1);
                 if (j + 1 == nseg) break;   // the last segment starts from this checkpoint
                 set_step_base(c, p * S + j * q);
-                GK_CUDA(cudaGraphLaunch(segment_graph(q, 0), s));
+                GK_CUDA(cudaGraphLaunch(segment_graph(q, 0, 0), s));
             }
         }
-        for (long long j = nseg - 1; j >= 0; --j) {
+        for (long long j = nseg - 1; j >= 0; --j, ++k) {
             const long long len = std::min(q, S - j * q);
+            const int b = (int)(k % nbuf);
+            if (k >= nbuf) GK_CUDA(cudaStreamWaitEvent(s, evR.ev[b], 0));
             load_state(segp + j * D1);
             set_step_base(c, p * S + j * q);
-            GK_CUDA(cudaGraphLaunch(segment_graph(len, mode), s));
+            GK_CUDA(cudaGraphLaunch(segment_graph(len, mode, b), s));
+            GK_CUDA(cudaEventRecord(evF.ev[b], s));
+            GK_CUDA(cudaStreamWaitEvent(s2, evF.ev[b], 0));
+            k_set_step<<<1, 1, 0, s2>>>(rbase.p, p * S + j * q);
+            GK_LAUNCH_CHECK();
+            GK_CUDA(cudaGraphLaunch(segment_graph(len, 3, b), s2));
+            GK_CUDA(cudaEventRecord(evR.ev[b], s2));
         }
     }
+    GK_CUDA(cudaStreamSynchronize(s2));
     // 3. loss and gradient, reduced in a fixed order
     std::vector<double> ho((size_t)S + 1), hp((size_t)grid * nslot);
     GK_CUDA(cudaMemcpyAsync(ho.data(), obs.p, sizeof(double) * (S + 1), cudaMemcpyDeviceToHost, s));

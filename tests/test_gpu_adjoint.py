@@ -32,13 +32,8 @@ def oracle_grad(d, S, period):
                               dK=[None, u.K1, None, None])
 
 
-@pytest.mark.parametrize("split", ["auto", "0"])
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
-def test_adjoint_vs_oracle(G, precision, tol, record, split, monkeypatch):
-    """N = 6 over 3 periods against the oracle's discrete adjoint, with the reverse stages in the
-    channel-split form (four lanes per row, the default for small systems) and without it."""
-    if split != "auto":
-        monkeypatch.setenv("GKSL_ADJ_SPLIT", split)
+def test_adjoint_vs_oracle(G, precision, tol, record):
     d = W.dimer(6)
     S, period = 60, 3
     ctx = G.dimer_context(d)
@@ -205,13 +200,10 @@ def test_autograd_function(G):
         G.gksl_destroy(ctx)
 
 
-@pytest.mark.parametrize("split", ["auto", "0"])
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
-def test_adjoint_ragged_segments_vs_oracle(G, precision, tol, record, split, monkeypatch):
+def test_adjoint_ragged_segments_vs_oracle(G, precision, tol, record):
     """S = 66 steps per period: the reverse sweep's checkpoint segments do not divide S, so the
-    last segment of every period is shorter than the others (split and unsplit reverse stages)."""
-    if split != "auto":
-        monkeypatch.setenv("GKSL_ADJ_SPLIT", split)
+    last segment of every period is shorter than the others."""
     d = W.dimer(5)
     S, period = 66, 2
     ctx = G.dimer_context(d)

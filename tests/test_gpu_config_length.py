@@ -109,12 +109,8 @@ def n50_oracle_gradient(G):
     return d, S, period, L, g
 
 
-@pytest.mark.parametrize("split", ["auto", "0"])
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
-def test_adjoint_n50_two_periods_vs_oracle_gradient(G, n50_oracle_gradient, precision, tol, record, split,
-                                                    monkeypatch):
-    if split != "auto":
-        monkeypatch.setenv("GKSL_ADJ_SPLIT", split)
+def test_adjoint_n50_two_periods_vs_oracle_gradient(G, n50_oracle_gradient, precision, tol, record):
     d, S, period, L, g = n50_oracle_gradient
     ctx = G.dimer_context(d)
     try:
