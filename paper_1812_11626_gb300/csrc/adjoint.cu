@@ -27,6 +27,7 @@
 // without room for every checkpoint); memory is periods * S/q state checkpoints (periods + S/q
 // without room) plus 4 q stage inputs.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -60,6 +61,7 @@ struct AdjArgs {
     long long n_long;
     int nb_long;
     long long D;
+    int pipe;    // four-channel slot loads issued together (ell_rows4), for small systems
 };
 
 // (C x)_r over the ELL slots of row r; the slot loads go out four at a time before their gathers
@@ -85,6 +87,63 @@ __device__ inline double ell_row(const HybView<VT> &H, long long r, const VT *__
         s += (double)__ldcs(H.ell_val + p) * (double)__ldg(x + __ldcs(H.ell_col + p));
     }
     return s;
+}
+
+// (C_c x)_r of four channels at once: the first four ELL slots of every channel are loaded
+// together (one round trip for up to 16 entries instead of one per channel), then each channel's
+// remaining slots four at a time.  Each channel's sum runs over its slots in the same order as
+// ell_row, so the results are the same bit for bit; it holds more registers, so it serves the
+// small systems whose rows leave most warp slots of the GPU empty.
+template <typename VT>
+__device__ inline void ell_rows4(const HybView<VT> *H, int nch, long long r, const VT *__restrict__ x,
+                                 double (&u)[4]) {
+    int cc[4][4];
+    VT vv[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool on = c < nch && j < H[c].width;
+            const long long p = (long long)j * H[c].ld + r;
+            cc[c][j] = on ? __ldcs(H[c].ell_col + p) : 0;
+            vv[c][j] = on ? __ldcs(H[c].ell_val + p) : VT(0);
+        }
+    VT xx[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xx[c][j] = (c < nch && j < H[c].width) ? __ldg(x + cc[c][j]) : VT(0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double s = 0.0;
+        if (c < nch) {
+            const int wd = H[c].width;
+            if (wd >= 4) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) s += (double)vv[c][j] * (double)xx[c][j];
+                int j = 4;
+                for (; j + 4 <= wd; j += 4) {
+                    int c4[4];
+                    VT v4[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const long long p = (long long)(j + k) * H[c].ld + r;
+                        c4[k] = __ldcs(H[c].ell_col + p);
+                        v4[k] = __ldcs(H[c].ell_val + p);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) s += (double)v4[k] * (double)__ldg(x + c4[k]);
+                }
+                for (; j < wd; ++j) {
+                    const long long p = (long long)j * H[c].ld + r;
+                    s += (double)__ldcs(H[c].ell_val + p) * (double)__ldg(x + __ldcs(H[c].ell_col + p));
+                }
+            } else {
+                for (int j = 0; j < wd; ++j) s += (double)vv[c][j] * (double)xx[c][j];
+            }
+        }
+        u[c] = s;
+    }
 }
 
 // (C x)_r of a long row by one warp: four entries per lane in flight, then a warp reduction
@@ -155,7 +214,7 @@ __device__ inline void adj_epilogue(const AdjArgs<VT> &a, long long r, double yb
 // collects x . K_q.  The constant factors of a launch (alpha = h/6 at stage 4, theta(t) of the
 // Q1 slot) are applied once per block when the partials go to this block's fixed slots of
 // `part`; the host maps slots to parameters.
-template <int STAGE, typename VT, int NC>
+template <int STAGE, typename VT, int NC, bool PIPE = false>
 __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *__restrict__ x,
                                                      const VT *__restrict__ Y, const double *lam, double *lacc,
                                                      VT *__restrict__ kb_out, const double *__restrict__ w,
@@ -204,8 +263,12 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
         const long long stride = (long long)(gridDim.x - a.nb_long) * nthr;
         for (long long r = (long long)(blockIdx.x - a.nb_long) * nthr + threadIdx.x; r < a.D; r += stride) {
             if (__ldcs(a.ch[0].ell_col + r) < 0) continue;   // long row, handled by a warp above
+            if constexpr (PIPE && NC == 4) {
+                ell_rows4<VT>(a.ch, a.nch, r, x, u);
+            } else {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) u[c] = c < a.nch ? ell_row<VT>(a.ch[c], r, x) : 0.0;
+                for (int c = 0; c < NC; ++c) u[c] = c < a.nch ? ell_row<VT>(a.ch[c], r, x) : 0.0;
+            }
             finish_row(r, u);
         }
     }
@@ -331,6 +394,15 @@ template <typename VT, int NC>
 void rev_stages_t(const AdjArgs<VT> &a, unsigned grid, int bt, cudaStream_t s, const VT *lam_in, const VT *Y1, const VT *Y2,
                   const VT *Y3, const VT *Y4, VT *ka, VT *kb, double *lam, double *lacc, const double *w,
                   double *part) {
+    if constexpr (NC == 4) {
+        if (a.pipe) {
+            k_adjoint<4, VT, 4, true><<<grid, bt, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
+            k_adjoint<3, VT, 4, true><<<grid, bt, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
+            k_adjoint<2, VT, 4, true><<<grid, bt, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
+            k_adjoint<1, VT, 4, true><<<grid, bt, 0, s>>>(a, ka, Y1, lam, lacc, nullptr, w, lam, part);
+            return;
+        }
+    }
     k_adjoint<4, VT, NC><<<grid, bt, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
     k_adjoint<3, VT, NC><<<grid, bt, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
     k_adjoint<2, VT, NC><<<grid, bt, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
@@ -422,6 +494,13 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
     GK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const AdjGrid ag = adj_grid(a64.n_long, D, sms);
     a64.nb_long = a32.nb_long = ag.nb_long;
+    // small systems (blocks already shrunk to 64 threads, few warps per SM): the reverse stages
+    // issue the four channels' first slots together; GKSL_ADJ_PIPE=0/1 forces it off/on
+    {
+        const char *env = getenv("GKSL_ADJ_PIPE");
+        const bool want = env ? env[0] == '1' : ag.threads <= 64;
+        a64.pipe = a32.pipe = (c->adj_n <= 4 && want) ? 1 : 0;
+    }
     const unsigned grid = ag.total;
     // channels compiled into the kernel: 4 (one dissipator, up to two H0 components), or all
     const int NC = c->adj_n <= 4 ? 4 : kMaxCh;

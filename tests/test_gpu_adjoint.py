@@ -32,8 +32,13 @@ def oracle_grad(d, S, period):
                               dK=[None, u.K1, None, None])
 
 
+@pytest.mark.parametrize("pipe", ["auto", "0"])
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
-def test_adjoint_vs_oracle(G, precision, tol, record):
+def test_adjoint_vs_oracle(G, precision, tol, record, pipe, monkeypatch):
+    """N = 6 over 3 periods against the oracle's discrete adjoint, with the four channels' first
+    slots loaded together in the reverse stages (the default for small systems) and without."""
+    if pipe != "auto":
+        monkeypatch.setenv("GKSL_ADJ_PIPE", pipe)
     d = W.dimer(6)
     S, period = 60, 3
     ctx = G.dimer_context(d)

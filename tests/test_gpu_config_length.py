@@ -109,8 +109,12 @@ def n50_oracle_gradient(G):
     return d, S, period, L, g
 
 
+@pytest.mark.parametrize("pipe", ["auto", "0"])
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
-def test_adjoint_n50_two_periods_vs_oracle_gradient(G, n50_oracle_gradient, precision, tol, record):
+def test_adjoint_n50_two_periods_vs_oracle_gradient(G, n50_oracle_gradient, precision, tol, record, pipe,
+                                                    monkeypatch):
+    if pipe != "auto":
+        monkeypatch.setenv("GKSL_ADJ_PIPE", pipe)
     d, S, period, L, g = n50_oracle_gradient
     ctx = G.dimer_context(d)
     try:
