@@ -224,9 +224,9 @@ gksl_status gksl_rho(gksl_ctx *ctx, const double *v, double *re, double *im);
  * grad receives n_grad doubles in the order [d/dA, d/dgamma_0 .. d/dgamma_{P-1},
  * d/dtheta_0 .. d/dtheta_{K-1}] over the set channels and components in index order.
  * Requires gksl_assemble with GKSL_ASM_TRANSPOSE.  The state is left unchanged.  For small
- * systems (at most 4 parameter channels, 64-thread reverse blocks) the reverse stages load the
- * channels' first slots together; the environment variable GKSL_ADJ_PIPE=0 turns that off (the
- * results are the same bit for bit). */
+ * systems (at most 4 parameter channels, 64-thread reverse blocks) the FP64 reverse stages load
+ * the channels' first slots together; the environment variable GKSL_ADJ_PIPE=0 or 1 turns that
+ * off or on in either precision (the results are the same bit for bit). */
 gksl_status gksl_adjoint_timeavg(gksl_ctx *ctx, const double *o_diag, long long steps_per_period,
                                  long long period_index, int precision, double *loss, double *grad, int n_grad);
 

@@ -32,7 +32,7 @@ def oracle_grad(d, S, period):
                               dK=[None, u.K1, None, None])
 
 
-@pytest.mark.parametrize("pipe", ["auto", "0"])
+@pytest.mark.parametrize("pipe", ["auto", "0", "1"])
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
 def test_adjoint_vs_oracle(G, precision, tol, record, pipe, monkeypatch):
     """N = 6 over 3 periods against the oracle's discrete adjoint, with the four channels' first
