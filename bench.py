@@ -277,6 +277,8 @@ def main():
                     help="profiling case for ncu: N=1000 assembly, then 50 FP64 and 50 FP32 RK4 steps")
     ap.add_argument("--profile-mf", action="store_true",
                     help="profiling case for ncu: the N=1000 matrix-free form, 20 FP64 and 20 FP32 RK4 steps")
+    ap.add_argument("--profile-adjoint-small", action="store_true",
+                    help="profiling case for ncu: the FP64 adjoint at N=200 over one period of 64 steps")
     ap.add_argument("--profile-dense", action="store_true",
                     help="profiling case for ncu: assembly of a dense L at N=100 (the dense dissipator route)")
     ap.add_argument("--profile-batch", action="store_true",
@@ -294,6 +296,9 @@ def main():
         return
     if args.profile_dense:
         run_profile_dense()
+        return
+    if args.profile_adjoint_small:
+        run_profile_adjoint(200)
         return
     if args.profile_batch:
         run_profile_batch()
@@ -582,17 +587,18 @@ def run_profile_batch():
         G.gksl_destroy(c)
 
 
-def run_profile_adjoint():
+def run_profile_adjoint(N=N_BENCH):
     """Small, fixed case for ncu: the FP64 adjoint of the N = 1000 dimer (every matrix stream
-    larger than L2, about 1.5 GB on the device) over one period of 64 steps.  The drive frequency
-    is raised so that 64 steps are the stable step count (h at the stability bound, as in the
-    full-size runs), which keeps the case short without changing any kernel's work per step."""
+    larger than L2, about 1.5 GB on the device), or of the N = 200 dimer of the adjoint workload,
+    over one period of 64 steps.  The drive frequency is raised so that 64 steps are the stable
+    step count (h at the stability bound, as in the full-size runs), which keeps the case short
+    without changing any kernel's work per step."""
     import __graft_entry__
     __graft_entry__.build()
     import numpy as np
     from paper_1812_11626_gb300 import gksl as G
     from paper_1812_11626_gb300 import workloads as W
-    d = W.dimer(N_BENCH)
+    d = W.dimer(N)
     ctx = G.dimer_context(d)
     spp = G.gksl_min_stable_steps(ctx)
     omega = d.params["omega"] * spp / 64.0
@@ -604,7 +610,7 @@ def run_profile_adjoint():
     t0 = time.perf_counter()
     loss = G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, 1, 64, grad)
     el = time.perf_counter() - t0
-    print(json.dumps({"profile_case": "adjoint N=1000", "steps_per_period": S, "omega": omega, "seconds": el,
+    print(json.dumps({"profile_case": f"adjoint N={N}", "steps_per_period": S, "omega": omega, "seconds": el,
                       "loss": loss, "grad": list(grad)}), flush=True)
     G.gksl_destroy(ctx)
 
