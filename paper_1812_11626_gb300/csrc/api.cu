@@ -353,15 +353,11 @@ extern "C" gksl_status gksl_set_kossakowski(gksl_ctx *c, const double *a_re, con
                     GK_REQUIRE(rr[j * D + j] >= -std::max(thr, 1e-12 * dmax0), GKSL_ERR_ARG,
                                "Kossakowski matrix is not positive semidefinite");
         }
-        c->km_A.release();
-        for (int p = 0; p < GKSL_MAX_P; ++p)
-            if (c->diss[p].set) c->diss[p] = Op();
-        c->comp_dirty = true;
-        c->assembled = false;
+        // dense route: necessary conditions of positive semidefiniteness, checked before the
+        // context changes (a rejected matrix leaves the previous channels in place)
+        double tr = 0.0;
         if (!low_rank) {
-            // dense route: necessary conditions of positive semidefiniteness, A kept whole
             const double eps = 1e-12 * mx;
-            double tr = 0.0;
             for (long long j = 0; j < D; ++j) {
                 GK_REQUIRE(ar[j * D + j] >= -eps, GKSL_ERR_ARG, "Kossakowski matrix is not positive semidefinite");
                 tr += ar[j * D + j];
@@ -373,6 +369,13 @@ extern "C" gksl_status gksl_set_kossakowski(gksl_ctx *c, const double *a_re, con
                     GK_REQUIRE(m2 <= dd + eps * mx * 4.0, GKSL_ERR_ARG,
                                "Kossakowski matrix is not positive semidefinite (a 2 x 2 principal minor is negative)");
                 }
+        }
+        c->km_A.release();
+        for (int p = 0; p < GKSL_MAX_P; ++p)
+            if (c->diss[p].set) c->diss[p] = Op();
+        c->comp_dirty = true;
+        c->assembled = false;
+        if (!low_rank) {   // A kept whole on the device, channel 0 at unit weight
             std::vector<double2> h(DD);
             for (size_t i = 0; i < DD; ++i) h[i] = make_double2(ar[i], ai[i]);
             c->km_A.alloc(DD);
