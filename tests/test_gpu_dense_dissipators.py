@@ -99,11 +99,15 @@ def test_kossakowski_full_rank_small_n_vs_eq8(G, N):
 
 def test_kossakowski_dense_route_rejects_indefinite(G):
     """On the dense route positive semidefiniteness is checked through the diagonal and the 2 x 2
-    principal minors: a negative diagonal entry and an oversized off-diagonal pair are rejected."""
+    principal minors: a negative diagonal entry and an oversized off-diagonal pair are rejected,
+    and a rejected matrix leaves the channels set before it untouched."""
     N = 9   # N > 64 is not needed: rank D > 8 sends any full-rank matrix to the dense route
     re, im = W.random_kossakowski(N, 5)
     ctx = G.gksl_create(N)
     try:
+        L = W.random_operator(N, 0.5, 6)
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 1, 0.3, op=L)   # kept if a matrix is rejected
+        G.gksl_set_drive(ctx, 0.0, 0.0, 1.0)
         bad = re.copy()
         bad[3, 3] = -1.0
         with pytest.raises(G.GkslError) as e:
@@ -113,6 +117,10 @@ def test_kossakowski_dense_route_rejects_indefinite(G):
         bad[1, 2] = bad[2, 1] = 10.0 * np.sqrt(re[1, 1] * re[2, 2])
         with pytest.raises(G.GkslError):
             G.gksl_set_kossakowski(ctx, bad, im)
+        # the rejected calls left the channel set before them in place
+        G.gksl_assemble(ctx, 0)
+        Rp, _ = OL.unfold_dense(np.zeros((N, N), complex), [L.to_dense()], [1.0])
+        assert np.abs(_csr(G, ctx, G.GKSL_MAT_R + 1).toarray() - Rp).max() < TOL_ASM * np.abs(Rp).max()
     finally:
         G.gksl_destroy(ctx)
 
