@@ -312,28 +312,12 @@ template <int STAGE, bool F64, bool PAIRS>
 __global__ void __launch_bounds__(kBThreads) k_batch_stage(BatchArgs a) {
     const long long step = *a.base + a.local;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // the tiles of the groups still running at this step, in group order, split into one
-    // contiguous range per CTA: neighbouring rows share most of their columns, so a CTA's
-    // gathers reuse what its SM's L1 already holds (a grid-stride walk spreads them over SMs)
-    long long active = 0;
-    for (int g = 0; g < a.ng; ++g)
-        if (step < a.gr[g].nsteps) active += a.gr[g].ntiles;
-    const long long per = (active + gridDim.x - 1) / gridDim.x;
-    const long long k0 = (long long)blockIdx.x * per, k1 = k0 + per < active ? k0 + per : active;
-    int gi = 0;
-    long long kk = k0;   // k0 as a tile index of group gi among the running groups
-    while (gi < a.ng && (step >= a.gr[gi].nsteps || kk >= a.gr[gi].ntiles)) {
-        if (step < a.gr[gi].nsteps) kk -= a.gr[gi].ntiles;
-        ++gi;
-    }
-    for (long long k = k0; k < k1; ++k, ++kk) {
-        while (gi < a.ng && (step >= a.gr[gi].nsteps || kk >= a.gr[gi].ntiles)) {
-            if (step < a.gr[gi].nsteps) kk -= a.gr[gi].ntiles;
-            ++gi;
-        }
-        if (gi >= a.ng) break;
+    for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        int gi = 0;
+        while (gi + 1 < a.ng && t >= a.gr[gi + 1].tile_begin) ++gi;
         const GroupDev &G = a.gr[gi];
-        const long long tl = kk;
+        if (step >= G.nsteps) continue;
+        long long tl = t - G.tile_begin;
         int ch = (int)(tl % G.nchunks);
         if constexpr (PAIRS && !F64) {
             if (G.pairs) {
