@@ -226,7 +226,11 @@ gksl_status gksl_rho(gksl_ctx *ctx, const double *v, double *re, double *im);
  * Requires gksl_assemble with GKSL_ASM_TRANSPOSE.  The state is left unchanged.  For small
  * systems (at most 4 parameter channels, 64-thread reverse blocks) the FP64 reverse stages load
  * the channels' first slots together; the environment variable GKSL_ADJ_PIPE=0 or 1 turns that
- * off or on in either precision (the results are the same bit for bit). */
+ * off or on in either precision (the results are the same bit for bit).  With at most 4 channels
+ * whose ELL slots total at most 32, the FP32 reverse stages load all of a row's slots at once
+ * and sum each channel in float (as the FP32 forward stage does; the FP64 stages sum in double);
+ * GKSL_ADJ_WIDE=0 or 1 turns that form off, or on in both precisions (in FP64 it gives the same
+ * results bit for bit as the channel-by-channel form). */
 gksl_status gksl_adjoint_timeavg(gksl_ctx *ctx, const double *o_diag, long long steps_per_period,
                                  long long period_index, int precision, double *loss, double *grad, int n_grad);
 

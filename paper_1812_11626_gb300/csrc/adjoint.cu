@@ -62,6 +62,14 @@ struct AdjArgs {
     int nb_long;
     long long D;
     int pipe;    // four-channel slot loads issued together (ell_rows4), for small systems
+    // wide form (k_adjoint_wide): the ELL blocks of the (at most four) channels stacked into
+    // one block of W_st slots, channel c's slot s at off[c] + s (off[c] = W_st past the last)
+    const int *st_col;
+    const VT *st_val;
+    long long ld_st;
+    int W_st;
+    int off[4];
+    int wm;   // host side: the kernel's slot capacity (0: k_adjoint)
 };
 
 // (C x)_r over the ELL slots of row r; the slot loads go out four at a time before their gathers
@@ -296,6 +304,129 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
     }
 }
 
+// One reverse stage of a system with at most four channels whose stacked ELL slots (all
+// channels' slots in one list, channel c's slot s at off[c] + s) number at most WM, one thread
+// per row.  Every slot load and the row's own operands (Y_r, x_r, K_q,r, lam_r, lacc_r) go out
+// at once, then every gather: two round trips to L2 per row instead of one pair per batch of four
+// slots.  The channel boundaries are the same for every row, so the per-channel sums switch at
+// fixed slots without divergence.  Each channel sums its slots in order in AT: double for the
+// FP64 stages, float for the FP32 ones (as the FP32 forward stage does); the gradient partials
+// and the stage outputs are formed in double.  Long rows go to warps as in k_adjoint.
+template <int STAGE, typename VT, typename AT, int WM>
+__global__ void __launch_bounds__(kThreads) k_adjoint_wide(AdjArgs<VT> a, const VT *__restrict__ x,
+                                                          const VT *__restrict__ Y, const double *lam, double *lacc,
+                                                          VT *__restrict__ kb_out, const double *__restrict__ w,
+                                                          double *lam_out, double *__restrict__ part) {
+    constexpr int NC = 4, NSLOT = 8;
+    const long long step = *a.base + a.local;
+    const double th = a.theta[3 * step + (STAGE == 1 ? 0 : (STAGE == 4 ? 2 : 1))];
+    const double alpha = STAGE == 4 ? a.h6 : 1.0;
+    double beta = 0.0;
+    if (STAGE == 1) {
+        const long long m = step - a.first;
+        beta = (m >= 0 && m < a.S) ? (m == 0 ? a.w_edge : a.w_mid) : 0.0;
+    }
+    double chw[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) chw[c] = c == a.q1ch ? a.E + a.A * th : (c < a.nch ? a.chw[c] : 0.0);
+    double g[NSLOT];
+#pragma unroll
+    for (int k = 0; k < NSLOT; ++k) g[k] = 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nthr = blockDim.x, nwarp = nthr >> 5;
+    // own-row part: gradient partials of row r and the stage outputs
+    auto finish_row = [&](long long r, const double (&u)[NC], double yr, double xr, const double (&kr)[NC],
+                          double lamr, double laccr, double wr) {
+        double ysum = 0.0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (c < a.nch) {
+                ysum += chw[c] * u[c];
+                g[c] += u[c] * yr;
+            }
+#pragma unroll
+        for (int q = 0; q < NC; ++q)
+            if (q < a.nkp) g[NC + q] += xr * kr[q];
+        const double ybar = alpha * ysum;
+        if (STAGE == 4) { kb_out[r] = (VT)(a.h3 * lamr + a.h * ybar); lacc[r] = lamr + ybar; }
+        if (STAGE == 3) { kb_out[r] = (VT)(a.h3 * lamr + a.h2 * ybar); lacc[r] = laccr + ybar; }
+        if (STAGE == 2) { kb_out[r] = (VT)(a.h6 * lamr + a.h2 * ybar); lacc[r] = laccr + ybar; }
+        if (STAGE == 1) lam_out[r] = laccr + ybar + beta * wr;
+    };
+    auto own_loads = [&](long long r, double &yr, double &xr, double (&kr)[NC], double &lamr, double &laccr,
+                         double &wr) {
+        yr = (double)Y[r];
+        xr = (double)x[r];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) kr[q] = q < a.nkp ? a.kp[q][r] : 0.0;
+        lamr = STAGE != 1 ? lam[r] : 0.0;
+        laccr = STAGE != 4 ? lacc[r] : 0.0;
+        wr = STAGE == 1 ? w[r] : 0.0;
+    };
+    if ((int)blockIdx.x < a.nb_long) {
+        for (long long i = (long long)blockIdx.x * nwarp + warp; i < a.n_long; i += (long long)a.nb_long * nwarp) {
+            double u[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) u[c] = c < a.nch ? tail_row<VT>(a.ch[c], i, lane, x) : 0.0;
+            if (lane == 0) {
+                const long long r = a.long_rows[i];
+                double yr, xr, kr[NC], lamr, laccr, wr;
+                own_loads(r, yr, xr, kr, lamr, laccr, wr);
+                finish_row(r, u, yr, xr, kr, lamr, laccr, wr);
+            }
+        }
+    } else {
+        const int W = a.W_st;
+        const int o1 = a.off[1], o2 = a.off[2], o3 = a.off[3];
+        const long long stride = (long long)(gridDim.x - a.nb_long) * nthr;
+        for (long long r = (long long)(blockIdx.x - a.nb_long) * nthr + threadIdx.x; r < a.D; r += stride) {
+            int cc[WM];
+            VT vv[WM];
+#pragma unroll
+            for (int k = 0; k < WM; ++k) {
+                const long long p = (long long)k * a.ld_st + r;
+                cc[k] = k < W ? __ldcs(a.st_col + p) : 0;
+                vv[k] = k < W ? __ldcs(a.st_val + p) : VT(0);
+            }
+            double yr, xr, kr[NC], lamr, laccr, wr;
+            own_loads(r, yr, xr, kr, lamr, laccr, wr);
+            if (cc[0] < 0) continue;   // channel 0, slot 0: -1 marks a long row, handled by a warp above
+            VT xx[WM];
+#pragma unroll
+            for (int k = 0; k < WM; ++k) xx[k] = k < W ? __ldg(x + cc[k]) : VT(0);
+            double u[NC] = {0.0, 0.0, 0.0, 0.0};
+            AT s = AT(0);
+            int cur = 0;
+#pragma unroll
+            for (int k = 0; k < WM; ++k)
+                if (k < W) {
+                    if (k == o1 || k == o2 || k == o3) {   // the same slots for every row
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) u[c] = c == cur ? (double)s : u[c];
+                        s = AT(0);
+                        ++cur;
+                    }
+                    s += (AT)vv[k] * (AT)xx[k];
+                }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) u[c] = c == cur ? (double)s : u[c];
+            finish_row(r, u, yr, xr, kr, lamr, laccr, wr);
+        }
+    }
+    __shared__ double red[kWarps][NSLOT];
+    warp_sum8(g, lane);
+    if ((lane & 3) == 0) red[warp][4 * (lane >> 4 & 1) + 2 * (lane >> 3 & 1) + (lane >> 2 & 1)] = g[0];
+    __syncthreads();
+    if (threadIdx.x < NSLOT) {
+        const int k = threadIdx.x;
+        double sum = 0.0;
+        for (int ww = 0; ww < nwarp; ++ww) sum += red[ww][k];
+        double f = alpha;
+        if (k == a.q1ch) f *= th;
+        part[(long long)blockIdx.x * NSLOT + k] += f * sum;
+    }
+}
+
 // blocks of one reverse stage: up to one per SM for the long rows (a warp each), then the ELL
 // rows (a thread each), both walked with a grid stride; at most 1024 threads per SM in all (the
 // register budget of the 4-channel kernel), so the whole grid is resident at once.  Blocks are
@@ -389,12 +520,32 @@ struct ExecSet {
     }
 };
 
+template <typename VT, int WM>
+void rev_wide(const AdjArgs<VT> &a, unsigned grid, int bt, cudaStream_t s, const VT *lam_in, const VT *Y1,
+              const VT *Y2, const VT *Y3, const VT *Y4, VT *ka, VT *kb, double *lam, double *lacc, const double *w,
+              double *part) {
+    using AT = VT;   // the FP32 stages sum in float, the FP64 ones in double
+    k_adjoint_wide<4, VT, AT, WM><<<grid, bt, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
+    k_adjoint_wide<3, VT, AT, WM><<<grid, bt, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
+    k_adjoint_wide<2, VT, AT, WM><<<grid, bt, 0, s>>>(a, kb, Y2, lam, lacc, ka, w, lam, part);
+    k_adjoint_wide<1, VT, AT, WM><<<grid, bt, 0, s>>>(a, ka, Y1, lam, lacc, nullptr, w, lam, part);
+}
+
 // the four reverse stages of one step: kb4 from lam', then kb3, kb2, and lam from kb1
 template <typename VT, int NC>
 void rev_stages_t(const AdjArgs<VT> &a, unsigned grid, int bt, cudaStream_t s, const VT *lam_in, const VT *Y1, const VT *Y2,
                   const VT *Y3, const VT *Y4, VT *ka, VT *kb, double *lam, double *lacc, const double *w,
                   double *part) {
     if constexpr (NC == 4) {
+        if (a.wm) {
+            switch (a.wm) {
+                case 8: rev_wide<VT, 8>(a, grid, bt, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part); break;
+                case 16: rev_wide<VT, 16>(a, grid, bt, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part); break;
+                case 24: rev_wide<VT, 24>(a, grid, bt, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part); break;
+                default: rev_wide<VT, 32>(a, grid, bt, s, lam_in, Y1, Y2, Y3, Y4, ka, kb, lam, lacc, w, part); break;
+            }
+            return;
+        }
         if (a.pipe) {
             k_adjoint<4, VT, 4, true><<<grid, bt, 0, s>>>(a, lam_in, Y4, lam, lacc, ka, w, lam, part);
             k_adjoint<3, VT, 4, true><<<grid, bt, 0, s>>>(a, ka, Y3, lam, lacc, kb, w, lam, part);
@@ -504,7 +655,60 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
         a64.pipe = (can && (env ? env[0] == '1' : ag.threads <= 64)) ? 1 : 0;
         a32.pipe = (can && env && env[0] == '1') ? 1 : 0;
     }
-    const unsigned grid = ag.total;
+    unsigned grid = ag.total;
+    int bt_rev = ag.threads;
+    // wide reverse stages (k_adjoint_wide) for systems with at most four channels whose rows fit
+    // in 32 stacked slots: the FP32 stages by default (N = 200, 300, 500: 16, 22, 12 % more
+    // gradient steps per second, mostly from summing in float), not the FP64 ones (N = 200: 17 %
+    // fewer; their FP64 chain, about 45 FP64 operations per row, then overlaps none of the
+    // loads).  GKSL_ADJ_WIDE=0/1 forces them off/on in both precisions where they apply.
+    DBuf<int> st_col;
+    DBuf<double> st_val64;
+    DBuf<float> st_val32;
+    {
+        const char *env = getenv("GKSL_ADJ_WIDE");
+        const bool on64 = env ? env[0] == '1' : false;
+        bool on = env ? env[0] == '1' : f32;
+        long long W = 0;
+        for (int i = 0; i < c->adj_n; ++i) {
+            W += c->adj[i].width;
+            if (c->adj[i].ld != c->adj[0].ld) on = false;
+        }
+        if (c->adj_n > 4 || W < 1 || W > 32) on = false;
+        if (on) {
+            const long long ld = c->adj[0].ld;
+            st_col.alloc((size_t)(W * ld));
+            if (on64) st_val64.alloc((size_t)(W * ld));
+            if (f32) st_val32.alloc((size_t)(W * ld));
+            int off[4];
+            long long o = 0;
+            for (int i = 0; i < 4; ++i) {
+                off[i] = (int)o;
+                if (i >= c->adj_n) continue;
+                const size_t n = (size_t)(c->adj[i].width * ld);
+                GK_CUDA(cudaMemcpyAsync(st_col.p + o * ld, c->adj[i].ell_col.p, sizeof(int) * n,
+                                        cudaMemcpyDeviceToDevice, s));
+                if (on64)
+                    GK_CUDA(cudaMemcpyAsync(st_val64.p + o * ld, c->adj[i].ell_val.p, sizeof(double) * n,
+                                            cudaMemcpyDeviceToDevice, s));
+                if (f32)
+                    GK_CUDA(cudaMemcpyAsync(st_val32.p + o * ld, c->adjf[i].ell_val.p, sizeof(float) * n,
+                                            cudaMemcpyDeviceToDevice, s));
+                o += c->adj[i].width;
+            }
+            const int wm = W <= 8 ? 8 : (W <= 16 ? 16 : (W <= 24 ? 24 : 32));
+            auto fill = [&](auto &a, const auto *val) {
+                a.wm = wm;
+                a.st_col = st_col.p;
+                a.st_val = val;
+                a.ld_st = ld;
+                a.W_st = (int)W;
+                for (int i = 0; i < 4; ++i) a.off[i] = off[i];
+            };
+            if (on64) fill(a64, st_val64.p);
+            if (f32) fill(a32, st_val32.p);
+        }
+    }
     // channels compiled into the kernel: 4 (one dissipator, up to two H0 components), or all
     const int NC = c->adj_n <= 4 ? 4 : kMaxCh;
     const int nslot = 2 * NC;
@@ -572,7 +776,7 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
             const float *Y1 = (const float *)Yp(b, 0, i), *Y2 = (const float *)Yp(b, 1, i),
                         *Y3 = (const float *)Yp(b, 2, i), *Y4 = (const float *)Yp(b, 3, i);
             float *ka = (float *)kbA.p, *kb = (float *)kbB.p;
-            rev_stages<float>(a, NC, grid, ag.threads, st, lamf.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p,
+            rev_stages<float>(a, NC, grid, bt_rev, st, lamf.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p,
                               part.p);
         } else {
             AdjArgs<double> a = a64;
@@ -580,7 +784,7 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
             const double *Y1 = (const double *)Yp(b, 0, i), *Y2 = (const double *)Yp(b, 1, i),
                          *Y3 = (const double *)Yp(b, 2, i), *Y4 = (const double *)Yp(b, 3, i);
             double *ka = (double *)kbA.p, *kb = (double *)kbB.p;
-            rev_stages<double>(a, NC, grid, ag.threads, st, lam.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p,
+            rev_stages<double>(a, NC, grid, bt_rev, st, lam.p, Y1, Y2, Y3, Y4, ka, kb, lam.p, lacc.p, w.p,
                                part.p);
         }
         GK_LAUNCH_CHECK();

@@ -32,13 +32,25 @@ def oracle_grad(d, S, period):
                               dK=[None, u.K1, None, None])
 
 
-@pytest.mark.parametrize("pipe", ["auto", "0", "1"])
+# forms of the reverse stage: the library's choice (FP32: all of a row's stacked channel slots
+# loaded at once and summed in float; FP64, small systems: the four channels' first slots loaded
+# together), one row per thread channel by channel, the latter with the first slots together, and
+# the wide form in both precisions
+FORMS = {"auto": {}, "rows": {"GKSL_ADJ_WIDE": "0", "GKSL_ADJ_PIPE": "0"},
+         "rows-pipe": {"GKSL_ADJ_WIDE": "0", "GKSL_ADJ_PIPE": "1"}, "wide": {"GKSL_ADJ_WIDE": "1"}}
+
+
+def set_form(monkeypatch, form):
+    for k, v in FORMS[form].items():
+        monkeypatch.setenv(k, v)
+
+
+@pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
-def test_adjoint_vs_oracle(G, precision, tol, record, pipe, monkeypatch):
-    """N = 6 over 3 periods against the oracle's discrete adjoint, with the four channels' first
-    slots loaded together in the reverse stages (the default for small systems) and without."""
-    if pipe != "auto":
-        monkeypatch.setenv("GKSL_ADJ_PIPE", pipe)
+def test_adjoint_vs_oracle(G, precision, tol, record, form, monkeypatch):
+    """N = 6 over 3 periods against the oracle's discrete adjoint, in every form of the reverse
+    stage."""
+    set_form(monkeypatch, form)
     d = W.dimer(6)
     S, period = 60, 3
     ctx = G.dimer_context(d)
@@ -274,6 +286,59 @@ def test_adjoint_general_operators_vs_oracle(G, precision, tol, record):
     L_ref, g_ref = OP.timeavg_adjoint(Q0, Q1, K, OP.eps_fn(E, A, omega), v0, w, c0, h, S, period,
                                       dQ0=[None, RK[0][0], RK[1][0]] + Qk, dQ1=[(Q1, sinw)] + [None] * 5,
                                       dK=[None, RK[0][1], RK[1][1]] + [None] * 3)
+    record("grad_max_abs_diff_vs_oracle_over_max", np.abs(grad - g_ref).max() / np.abs(g_ref).max())
+    assert abs(loss - L_ref) < (1e-11 if precision == 64 else 1e-4) * max(1.0, abs(L_ref))
+    assert np.abs(grad - g_ref).max() < tol * np.abs(g_ref).max(), (grad, g_ref)
+
+
+@pytest.mark.parametrize("N", [3, 6])
+@pytest.mark.parametrize("form", ["auto", "rows", "wide"])
+@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
+def test_adjoint_dense_four_channels_vs_oracle(G, N, precision, tol, record, form, monkeypatch):
+    """Two dense H0 components, a dense drive operator and one dense traceful dissipator: four
+    gradient channels whose rows hold up to D entries each.  At N = 3 (D = 8) the four channels'
+    slots together fill the wide reverse stage's largest form (up to 32 stacked slots); at
+    N = 6 (D = 35) they exceed it and the library keeps the channel-by-channel form."""
+    from oracle import basis as OB
+    from oracle import lindblad as LB
+    set_form(monkeypatch, form)
+    Hs = [W.random_operator(N, 1.0, 60 + k, hermitian=True) for k in range(2)]
+    H1 = W.random_operator(N, 1.0, 62, hermitian=True)
+    L = W.random_operator(N, 1.0, 63)
+    theta, gam = [0.5, -0.8], 0.2
+    E, A, omega = 0.2, 0.6, 3.0
+    S, period = 120, 2
+    o_diag = np.linspace(1.0, -1.0, N)
+    rho0 = np.diag(np.linspace(2, 1, N)).astype(complex)
+    rho0 /= np.trace(rho0)
+    rho0[0, N - 1] = 0.03 - 0.04j
+    rho0[N - 1, 0] = np.conj(rho0[0, N - 1])
+    ctx = G.gksl_create(N)
+    try:
+        for k, (th, H) in enumerate(zip(theta, Hs)):
+            G.set_csr_operator(G.gksl_set_h0_component, ctx, k, th, op=H)
+        G.set_csr_operator(G.gksl_set_h1, ctx, op=H1)
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, gam, op=L)
+        G.gksl_set_drive(ctx, E, A, omega)
+        G.gksl_assemble(ctx, G.GKSL_ASM_FP32 | G.GKSL_ASM_TRANSPOSE)
+        assert G.gksl_min_stable_steps(ctx) <= S
+        G.gksl_set_rho0(ctx, rho0.real.copy(), rho0.imag.copy())
+        grad = np.zeros(4)   # [A, gamma_0, theta_0, theta_1]
+        loss = G.gksl_adjoint_timeavg(ctx, o_diag, S, period, precision, grad)
+    finally:
+        G.gksl_destroy(ctx)
+    Z = np.zeros((N, N))
+    Qk = [LB.unfold_dense(H.to_dense())[0] for H in Hs]
+    Q1 = LB.unfold_dense(H1.to_dense())[0]
+    R, K = LB.unfold_dense(Z, [L.to_dense()], [1.0])
+    Q0 = sum(th * Q for th, Q in zip(theta, Qk)) + gam * R
+    w, c0 = OP.observable_weights(o_diag)
+    v0 = OB.expand(rho0).real
+    h = 2 * np.pi / omega / S
+    sinw = lambda t: np.sin(omega * t)
+    L_ref, g_ref = OP.timeavg_adjoint(Q0, Q1, gam * K, OP.eps_fn(E, A, omega), v0, w, c0, h, S, period,
+                                      dQ0=[None, R] + Qk, dQ1=[(Q1, sinw), None, None, None],
+                                      dK=[None, K, None, None])
     record("grad_max_abs_diff_vs_oracle_over_max", np.abs(grad - g_ref).max() / np.abs(g_ref).max())
     assert abs(loss - L_ref) < (1e-11 if precision == 64 else 1e-4) * max(1.0, abs(L_ref))
     assert np.abs(grad - g_ref).max() < tol * np.abs(g_ref).max(), (grad, g_ref)

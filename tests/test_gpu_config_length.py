@@ -109,12 +109,15 @@ def n50_oracle_gradient(G):
     return d, S, period, L, g
 
 
-@pytest.mark.parametrize("pipe", ["auto", "0"])
+@pytest.mark.parametrize("form", ["auto", "rows", "wide"])
 @pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
-def test_adjoint_n50_two_periods_vs_oracle_gradient(G, n50_oracle_gradient, precision, tol, record, pipe,
+def test_adjoint_n50_two_periods_vs_oracle_gradient(G, n50_oracle_gradient, precision, tol, record, form,
                                                     monkeypatch):
-    if pipe != "auto":
-        monkeypatch.setenv("GKSL_ADJ_PIPE", pipe)
+    # reverse-stage forms: the library's choice, channel by channel, and all of a row's stacked
+    # slots loaded at once in both precisions
+    env = {"auto": {}, "rows": {"GKSL_ADJ_WIDE": "0", "GKSL_ADJ_PIPE": "0"}, "wide": {"GKSL_ADJ_WIDE": "1"}}
+    for k, v in env[form].items():
+        monkeypatch.setenv(k, v)
     d, S, period, L, g = n50_oracle_gradient
     ctx = G.dimer_context(d)
     try:
