@@ -443,6 +443,22 @@ def main():
             for i, p in enumerate(("fp64", "fp32"))}
         extras["stage_columns_16bit"] = {"escaped_rows": tinfo.compact_escaped_rows, "long_rows": tinfo.long_rows,
                                          "long_row_entries": tinfo.tail_nnz}
+        # the FP32 stage against HBM by its own bytes: the form in use (timed above), and the fastest
+        # variant of each column width as the variant timer measured it (8-step graphs, warm)
+        extras["fp32_bulk"]["frac_of_hbm"] = extras["fp32_bulk"]["achieved_gbs"] / hbm
+        by_form = {}
+        for name, us, wide in (("32-bit columns", tinfo.rk4_variant_us[1], None),
+                               ("16-bit columns", tinfo.rk4_variant_us_c16[1],
+                                tinfo.tail_nnz + tinfo.compact_escaped_rows * tinfo.ell_width_q0)):
+            timed = [(x, v) for v, x in enumerate(us) if x > 0]
+            if not timed:
+                continue
+            t_us, var = min(timed)
+            b = stage_bytes(tinfo.nnz_q0, tinfo.nnz_q1, D, 32, bool(tinfo.q1_folded), wide)
+            gbs = 4 * b / (t_us * 1e-6) / 1e9
+            by_form[name] = {"variant": var, "us_per_step": t_us, "algorithmic_bytes_per_launch": b,
+                             "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm}
+        extras["fp32_bulk"]["by_column_form"] = by_form
     G.gksl_destroy(ctx)
     if not args.no_extras and rank == 0:
         extras["matrix_free"] = matrix_free_extras(G, W, torch, stream, d, spp, args.steps)

@@ -342,3 +342,64 @@ def test_adjoint_dense_four_channels_vs_oracle(G, N, precision, tol, record, for
     record("grad_max_abs_diff_vs_oracle_over_max", np.abs(grad - g_ref).max() / np.abs(g_ref).max())
     assert abs(loss - L_ref) < (1e-11 if precision == 64 else 1e-4) * max(1.0, abs(L_ref))
     assert np.abs(grad - g_ref).max() < tol * np.abs(g_ref).max(), (grad, g_ref)
+
+
+@pytest.mark.parametrize("with_l", [False, True], ids=["h0_h1", "h0_h1_l"])
+@pytest.mark.parametrize("form", ["auto", "rows", "wide"])
+@pytest.mark.parametrize("precision,tol", [(64, 1e-9), (32, 1e-5)])
+def test_adjoint_fewer_channels_vs_oracle(G, with_l, precision, tol, record, form, monkeypatch):
+    """One H0 component and a drive operator, with and without one dissipator (two or three
+    gradient channels, fewer than the four-channel kernels hold, and no K column without the
+    dissipator) at N = 4, against the oracle's discrete adjoint in every form of the reverse stage."""
+    from oracle import basis as OB
+    from oracle import lindblad as LB
+    set_form(monkeypatch, form)
+    N = 4
+    # rows of at most 5, 3 and 7 entries: 8 stacked slots without the dissipator (the smallest
+    # wide form, full), 15 with it
+    H = W.random_operator(N, 0.2, 70, hermitian=True)
+    H1 = W.random_operator(N, 0.2, 71, hermitian=True)
+    L = W.random_operator(N, 0.2, 72)
+    theta, gam = 0.9, 0.25
+    E, A, omega = 0.4, 0.7, 2.5
+    S, period = 80, 2
+    o_diag = np.linspace(0.5, -1.5, N)
+    rho0 = np.diag(np.linspace(3, 1, N)).astype(complex)
+    rho0 /= np.trace(rho0)
+    rho0[1, 2] = 0.04 + 0.01j
+    rho0[2, 1] = np.conj(rho0[1, 2])
+    ctx = G.gksl_create(N)
+    try:
+        G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, theta, op=H)
+        G.set_csr_operator(G.gksl_set_h1, ctx, op=H1)
+        if with_l:
+            G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, gam, op=L)
+        G.gksl_set_drive(ctx, E, A, omega)
+        G.gksl_assemble(ctx, G.GKSL_ASM_FP32 | G.GKSL_ASM_TRANSPOSE)
+        assert G.gksl_min_stable_steps(ctx) <= S
+        G.gksl_set_rho0(ctx, rho0.real.copy(), rho0.imag.copy())
+        grad = np.zeros(3 if with_l else 2)   # [A, (gamma_0,) theta_0]
+        loss = G.gksl_adjoint_timeavg(ctx, o_diag, S, period, precision, grad)
+    finally:
+        G.gksl_destroy(ctx)
+    Z = np.zeros((N, N))
+    Qh = LB.unfold_dense(H.to_dense())[0]
+    Q1 = LB.unfold_dense(H1.to_dense())[0]
+    D = N * N - 1
+    if with_l:
+        R, K = LB.unfold_dense(Z, [L.to_dense()], [1.0])
+        Q0, Kv = theta * Qh + gam * R, gam * K
+        dQ0, dK = [None, R, Qh], [None, K, None]
+    else:
+        Q0, Kv = theta * Qh, np.zeros(D)
+        dQ0, dK = [None, Qh], [None, None]
+    sinw = lambda t: np.sin(omega * t)
+    dQ1 = [(Q1, sinw)] + [None] * (len(dQ0) - 1)
+    w, c0 = OP.observable_weights(o_diag)
+    v0 = OB.expand(rho0).real
+    h = 2 * np.pi / omega / S
+    L_ref, g_ref = OP.timeavg_adjoint(Q0, Q1, Kv, OP.eps_fn(E, A, omega), v0, w, c0, h, S, period,
+                                      dQ0=dQ0, dQ1=dQ1, dK=dK)
+    record("grad_max_abs_diff_vs_oracle_over_max", np.abs(grad - g_ref).max() / np.abs(g_ref).max())
+    assert abs(loss - L_ref) < (1e-11 if precision == 64 else 1e-4) * max(1.0, abs(L_ref))
+    assert np.abs(grad - g_ref).max() < tol * np.abs(g_ref).max(), (grad, g_ref)
