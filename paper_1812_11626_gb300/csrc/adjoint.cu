@@ -311,9 +311,12 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
 // slots.  The channel boundaries are the same for every row, so the per-channel sums switch at
 // fixed slots without divergence.  Each channel sums its slots in order in AT: double for the
 // FP64 stages, float for the FP32 ones (as the FP32 forward stage does); the gradient partials
-// and the stage outputs are formed in double.  Long rows go to warps as in k_adjoint.
+// and the stage outputs are formed in double.  Long rows go to warps as in k_adjoint.  The FP32
+// instances are held to two 256-thread blocks per SM (128 registers, a few dozen bytes spilled
+// at 24 slots): at N = 1000 that takes a period-2 gradient from 754 to 609 us per step, and
+// N = 200 does not move.
 template <int STAGE, typename VT, typename AT, int WM>
-__global__ void __launch_bounds__(kThreads) k_adjoint_wide(AdjArgs<VT> a, const VT *__restrict__ x,
+__global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 2 : 1) k_adjoint_wide(AdjArgs<VT> a, const VT *__restrict__ x,
                                                           const VT *__restrict__ Y, const double *lam, double *lacc,
                                                           VT *__restrict__ kb_out, const double *__restrict__ w,
                                                           double *lam_out, double *__restrict__ part) {
