@@ -279,6 +279,8 @@ def main():
                     help="profiling case for ncu: the N=1000 matrix-free form, 20 FP64 and 20 FP32 RK4 steps")
     ap.add_argument("--profile-adjoint-small", action="store_true",
                     help="profiling case for ncu: the FP64 adjoint at N=200 over one period of 64 steps")
+    ap.add_argument("--profile-adjoint-small-fp32", action="store_true",
+                    help="profiling case for ncu: the same with the FP32 adjoint (its wide reverse stages)")
     ap.add_argument("--profile-dense", action="store_true",
                     help="profiling case for ncu: assembly of a dense L at N=100 (the dense dissipator route)")
     ap.add_argument("--profile-batch", action="store_true",
@@ -299,6 +301,9 @@ def main():
         return
     if args.profile_adjoint_small:
         run_profile_adjoint(200)
+        return
+    if args.profile_adjoint_small_fp32:
+        run_profile_adjoint(200, 32)
         return
     if args.profile_batch:
         run_profile_batch()
@@ -603,10 +608,10 @@ def run_profile_batch():
         G.gksl_destroy(c)
 
 
-def run_profile_adjoint(N=N_BENCH):
-    """Small, fixed case for ncu: the FP64 adjoint of the N = 1000 dimer (every matrix stream
-    larger than L2, about 1.5 GB on the device), or of the N = 200 dimer of the adjoint workload,
-    over one period of 64 steps.  The drive frequency is raised so that 64 steps are the stable
+def run_profile_adjoint(N=N_BENCH, precision=64):
+    """Small, fixed case for ncu: the FP64 (or FP32) adjoint of the N = 1000 dimer (every matrix
+    stream larger than L2, about 1.5 GB on the device), or of the N = 200 dimer of the adjoint
+    workload, over one period of 64 steps.  The drive frequency is raised so that 64 steps are the stable
     step count (h at the stability bound, as in the full-size runs), which keeps the case short
     without changing any kernel's work per step."""
     import __graft_entry__
@@ -624,9 +629,10 @@ def run_profile_adjoint(N=N_BENCH):
     S = G.gksl_min_stable_steps(ctx)
     grad = np.zeros(4)
     t0 = time.perf_counter()
-    loss = G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, 1, 64, grad)
+    loss = G.gksl_adjoint_timeavg(ctx, d.obs_diag, S, 1, precision, grad)
     el = time.perf_counter() - t0
-    print(json.dumps({"profile_case": f"adjoint N={N}", "steps_per_period": S, "omega": omega, "seconds": el,
+    print(json.dumps({"profile_case": f"adjoint N={N} FP{precision}", "steps_per_period": S, "omega": omega,
+                      "seconds": el,
                       "loss": loss, "grad": list(grad)}), flush=True)
     G.gksl_destroy(ctx)
 
