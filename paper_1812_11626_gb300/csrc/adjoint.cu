@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
 #pragma unroll
         for (int c = 0; c < NC; ++c)
             if (c < a.nch) {
-                ysum += chw[c] * u[c];
-                g[c] += u[c] * yr;
+                ysum += chw[c] * (double)u[c];
+                g[c] += (double)u[c] * yr;
             }
         const double xr = (double)x[r];
 #pragma unroll
@@ -310,11 +310,13 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
 // at once, then every gather: two round trips to L2 per row instead of one pair per batch of four
 // slots.  The channel boundaries are the same for every row, so the per-channel sums switch at
 // fixed slots without divergence.  Each channel sums its slots in order in AT: double for the
-// FP64 stages, float for the FP32 ones (as the FP32 forward stage does); the gradient partials
-// and the stage outputs are formed in double.  Long rows go to warps as in k_adjoint.  The FP32
+// FP64 stages, float for the FP32 ones (as the FP32 forward stage does).  The FP64 stages form
+// the weighted sum, the gradient partials and the stage outputs in double; the FP32 stages form
+// the weighted sum and this thread's channel partials in float (converted once per thread before
+// the block sums) and only the updates of the adjoint state in double.  Long rows go to warps as in k_adjoint.  The FP32
 // instances are held to two 256-thread blocks per SM (128 registers, a few dozen bytes spilled
 // at 24 slots): at N = 1000 that takes a period-2 gradient from 754 to 609 us per step, and
-// N = 200 does not move.
+// N = 200 does not move; the weighting and partials in float take it on to 504 us.
 template <int STAGE, typename VT, typename AT, int WM>
 __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 2 : 1) k_adjoint_wide(AdjArgs<VT> a, const VT *__restrict__ x,
                                                           const VT *__restrict__ Y, const double *lam, double *lacc,
@@ -335,10 +337,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 2 : 1) k_adjoint_w
     double g[NSLOT];
 #pragma unroll
     for (int k = 0; k < NSLOT; ++k) g[k] = 0.0;
+    float chwf[NC], gf[NC];   // FP32 stages: the weights in float, this thread's channel partials
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        chwf[c] = (float)chw[c];
+        gf[c] = 0.0f;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nthr = blockDim.x, nwarp = nthr >> 5;
     // own-row part: gradient partials of row r and the stage outputs
-    auto finish_row = [&](long long r, const double (&u)[NC], double yr, double xr, const double (&kr)[NC],
+    auto finish_row = [&](long long r, const auto (&u)[NC], double yr, double xr, const double (&kr)[NC],
                           double lamr, double laccr, double wr) {
         double ysum = 0.0;
 #pragma unroll
@@ -397,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 2 : 1) k_adjoint_w
             VT xx[WM];
 #pragma unroll
             for (int k = 0; k < WM; ++k) xx[k] = k < W ? __ldg(x + cc[k]) : VT(0);
-            double u[NC] = {0.0, 0.0, 0.0, 0.0};
+            AT uc[NC] = {AT(0), AT(0), AT(0), AT(0)};
             AT s = AT(0);
             int cur = 0;
 #pragma unroll
@@ -405,17 +413,40 @@ __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 2 : 1) k_adjoint_w
                 if (k < W) {
                     if (k == o1 || k == o2 || k == o3) {   // the same slots for every row
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) u[c] = c == cur ? (double)s : u[c];
+                        for (int c = 0; c < NC; ++c) uc[c] = c == cur ? s : uc[c];
                         s = AT(0);
                         ++cur;
                     }
                     s += (AT)vv[k] * (AT)xx[k];
                 }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) u[c] = c == cur ? (double)s : u[c];
-            finish_row(r, u, yr, xr, kr, lamr, laccr, wr);
+            for (int c = 0; c < NC; ++c) uc[c] = c == cur ? s : uc[c];
+            if constexpr (sizeof(AT) == 8) {
+                finish_row(r, uc, yr, xr, kr, lamr, laccr, wr);
+            } else {
+                // FP32 stages: the channel weighting and the gradient partials in float too (one
+                // conversion per row for the weighted sum), only the adjoint state in double
+                const float yf = Y[r];
+                float ys = 0.0f;
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (c < a.nch) {
+                        ys = fmaf(chwf[c], uc[c], ys);
+                        gf[c] = fmaf(uc[c], yf, gf[c]);
+                    }
+#pragma unroll
+                for (int q = 0; q < NC; ++q)
+                    if (q < a.nkp) g[NC + q] += xr * kr[q];
+                const double ybar = alpha * (double)ys;
+                if (STAGE == 4) { kb_out[r] = (VT)(a.h3 * lamr + a.h * ybar); lacc[r] = lamr + ybar; }
+                if (STAGE == 3) { kb_out[r] = (VT)(a.h3 * lamr + a.h2 * ybar); lacc[r] = laccr + ybar; }
+                if (STAGE == 2) { kb_out[r] = (VT)(a.h6 * lamr + a.h2 * ybar); lacc[r] = laccr + ybar; }
+                if (STAGE == 1) lam_out[r] = laccr + ybar + beta * wr;
+            }
         }
     }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) g[c] += (double)gf[c];
     __shared__ double red[kWarps][NSLOT];
     warp_sum8(g, lane);
     if ((lane & 3) == 0) red[warp][4 * (lane >> 4 & 1) + 2 * (lane >> 3 & 1) + (lane >> 2 & 1)] = g[0];
