@@ -70,6 +70,7 @@ struct AdjArgs {
     int W_st;
     int off[4];
     int wm;   // host side: the kernel's slot capacity (0: k_adjoint)
+    float chwf[4], Ef, Af;   // the channel weights and E, A in float (the wide FP32 stages)
 };
 
 // (C x)_r over the ELL slots of row r; the slot loads go out four at a time before their gathers
@@ -180,25 +181,26 @@ __device__ inline double tail_row(const HybView<VT> &H, long long i, int lane, c
 // a lane keeps (bits 16, 8, 4 of the lane index pick the half), the last two rounds finish the
 // sum inside groups of four lanes.  Afterwards lane l holds the sum of slot
 // 4 (l >> 4 & 1) + 2 (l >> 3 & 1) + (l >> 2 & 1) in v[0].
-__device__ inline void warp_sum8(double v[8], int lane) {
+template <typename T>
+__device__ inline void warp_sum8(T v[8], int lane) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool hi = lane & 16;
-        const double send = hi ? v[k] : v[k + 4];
-        const double keep = hi ? v[k + 4] : v[k];
+        const T send = hi ? v[k] : v[k + 4];
+        const T keep = hi ? v[k + 4] : v[k];
         v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const bool hi = lane & 8;
-        const double send = hi ? v[k] : v[k + 2];
-        const double keep = hi ? v[k + 2] : v[k];
+        const T send = hi ? v[k] : v[k + 2];
+        const T keep = hi ? v[k + 2] : v[k];
         v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
     {
         const bool hi = lane & 4;
-        const double send = hi ? v[0] : v[1];
-        const double keep = hi ? v[1] : v[0];
+        const T send = hi ? v[0] : v[1];
+        const T keep = hi ? v[1] : v[0];
         v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
     }
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
@@ -312,8 +314,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs<VT> a, const VT *_
 // fixed slots without divergence.  Each channel sums its slots in order in AT: double for the
 // FP64 stages, float for the FP32 ones (as the FP32 forward stage does).  The FP64 stages form
 // the weighted sum, the gradient partials and the stage outputs in double; the FP32 stages form
-// the weighted sum and this thread's channel partials in float (converted once per thread before
-// the block sums) and only the updates of the adjoint state in double.  Long rows go to warps as in k_adjoint.  The FP32
+// the weighted sum, this thread's gradient partials and their warp sums in float and only the
+// updates of the adjoint state, and the sums over warps and blocks, in double.  Long rows go to warps as in k_adjoint.  The FP32
 // instances are held to two 256-thread blocks per SM (128 registers, a few dozen bytes spilled
 // at 24 slots): at N = 1000 that takes a period-2 gradient from 754 to 609 us per step, and
 // N = 200 does not move; the weighting and partials in float take it on to 504 us.
@@ -337,12 +339,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 2 : 1) k_adjoint_w
     double g[NSLOT];
 #pragma unroll
     for (int k = 0; k < NSLOT; ++k) g[k] = 0.0;
-    float chwf[NC], gf[NC];   // FP32 stages: the weights in float, this thread's channel partials
+    // FP32 stages: the weights in float (the drive's from theta in float), and this thread's
+    // partials of the ELL rows in float
+    float chwf[NC], gf[NSLOT];
+    if constexpr (sizeof(AT) == 4) {
+        const float thf = (float)th;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        chwf[c] = (float)chw[c];
-        gf[c] = 0.0f;
+        for (int c = 0; c < NC; ++c) chwf[c] = c == a.q1ch ? fmaf(a.Af, thf, a.Ef) : a.chwf[c];
     }
+#pragma unroll
+    for (int k = 0; k < NSLOT; ++k) gf[k] = 0.0f;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nthr = blockDim.x, nwarp = nthr >> 5;
     // own-row part: gradient partials of row r and the stage outputs
@@ -426,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 2 : 1) k_adjoint_w
             } else {
                 // FP32 stages: the channel weighting and the gradient partials in float too (one
                 // conversion per row for the weighted sum), only the adjoint state in double
-                const float yf = Y[r];
+                const float yf = Y[r], xf = x[r];
                 float ys = 0.0f;
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
@@ -436,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 2 : 1) k_adjoint_w
                     }
 #pragma unroll
                 for (int q = 0; q < NC; ++q)
-                    if (q < a.nkp) g[NC + q] += xr * kr[q];
+                    if (q < a.nkp) gf[NC + q] = fmaf(xf, (float)kr[q], gf[NC + q]);
                 const double ybar = alpha * (double)ys;
                 if (STAGE == 4) { kb_out[r] = (VT)(a.h3 * lamr + a.h * ybar); lacc[r] = lamr + ybar; }
                 if (STAGE == 3) { kb_out[r] = (VT)(a.h3 * lamr + a.h2 * ybar); lacc[r] = laccr + ybar; }
@@ -445,11 +451,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 2 : 1) k_adjoint_w
             }
         }
     }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) g[c] += (double)gf[c];
+    // warp sums of the partials: in float for the ELL blocks of the FP32 stages (their partials are
+    // all in gf), in double otherwise; one value per slot and warp, kept in double
     __shared__ double red[kWarps][NSLOT];
-    warp_sum8(g, lane);
-    if ((lane & 3) == 0) red[warp][4 * (lane >> 4 & 1) + 2 * (lane >> 3 & 1) + (lane >> 2 & 1)] = g[0];
+    const int slot = 4 * (lane >> 4 & 1) + 2 * (lane >> 3 & 1) + (lane >> 2 & 1);
+    if (sizeof(AT) == 4 && (int)blockIdx.x >= a.nb_long) {
+        warp_sum8(gf, lane);
+        if ((lane & 3) == 0) red[warp][slot] = (double)gf[0];
+    } else {
+        warp_sum8(g, lane);
+        if ((lane & 3) == 0) red[warp][slot] = g[0];
+    }
     __syncthreads();
     if (threadIdx.x < NSLOT) {
         const int k = threadIdx.x;
@@ -733,6 +745,9 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
             const int wm = W <= 8 ? 8 : (W <= 16 ? 16 : (W <= 24 ? 24 : 32));
             auto fill = [&](auto &a, const auto *val) {
                 a.wm = wm;
+                for (int i = 0; i < 4; ++i) a.chwf[i] = i < a.nch ? (float)a.chw[i] : 0.0f;
+                a.Ef = (float)a.E;
+                a.Af = (float)a.A;
                 a.st_col = st_col.p;
                 a.st_val = val;
                 a.ld_st = ld;
