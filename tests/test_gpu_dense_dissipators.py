@@ -217,3 +217,29 @@ def test_kossakowski_full_rank_n100_vs_eq8_columns(G, record):
         assert np.linalg.eigvalsh(rho).min() > -1e-8
     finally:
         G.gksl_destroy(ctx)
+
+
+def test_dense_routes_reject_sizes_past_their_limits(G):
+    """The dense dissipator route holds R as D^2 < 2^31 entries (N <= 200) and the Kossakowski form
+    holds the kernel M of N^4 complex entries (N <= 128).  Past those sizes the calls return
+    GKSL_ERR_ARG before reading or allocating anything, and the context stays usable: at N = 201
+    the sparse route still assembles the same operators."""
+    N = 201
+    d = W.dimer(N)
+    ctx = G.dimer_context(d, assemble=False)
+    try:
+        with pytest.raises(G.GkslError) as e:
+            G.gksl_assemble(ctx, G.GKSL_ASM_DENSE_DISSIPATORS)
+        assert e.value.status == G.GKSL_ERR_ARG and "N <= 200" in str(e.value)
+        G.gksl_assemble(ctx, 0)
+        assert G.gksl_get_info(ctx).nnz_q0 > 0
+    finally:
+        G.gksl_destroy(ctx)
+    ctx = G.gksl_create(129)
+    try:
+        with pytest.raises(G.GkslError) as e:
+            # the size is checked before A is read, so a placeholder array suffices
+            G.gksl_set_kossakowski(ctx, np.zeros(1))
+        assert e.value.status == G.GKSL_ERR_ARG and "N <= 128" in str(e.value)
+    finally:
+        G.gksl_destroy(ctx)
