@@ -299,13 +299,31 @@ extern "C" gksl_status gksl_set_drive(gksl_ctx *c, double E, double A, double om
 // l_p = c_p / |c_p|, L_p = sum_j l_pj F_j.  Any such rank factorisation gives the same Lindbladian
 // as the eigen-decomposition of Eq. 9 (the dissipator is invariant under a unitary remixing of its
 // channels).  A matrix of higher rank, or any A at N > 64, is kept whole on the device and
-// assembled by the dense route (dense_diss.cu) as channel 0 at unit weight.
+// assembled by the dense route (dense_diss.cu) as channel 0 at unit weight; at N > 64 it is
+// copied and checked on the device (kossakowski_upload_checked), below on the host.
 extern "C" gksl_status gksl_set_kossakowski(gksl_ctx *c, const double *a_re, const double *a_im, double tol) {
     return guarded(c, [&] {
         GK_REQUIRE(a_re && tol >= 0.0, GKSL_ERR_ARG, "a_re must not be null and tol >= 0");
         const long long D = c->D;
         const int N = c->N;
         GK_REQUIRE(N <= kDenseKmMaxN, GKSL_ERR_ARG, "the Kossakowski form is limited to N <= 128");
+        if (N > 64) {
+            // dense route without a rank factorisation: the matrix goes to the device and is
+            // checked there (the same conditions and messages as below), then replaces the channels
+            DBuf<double2> A;
+            const double tr = kossakowski_upload_checked(c, a_re, a_im, A);
+            for (int p = 0; p < GKSL_MAX_P; ++p)
+                if (c->diss[p].set) c->diss[p] = Op();
+            c->km_A = std::move(A);
+            c->comp_dirty = true;
+            c->assembled = false;
+            Op &o = c->diss[0];
+            o.set = true;
+            o.km = true;
+            o.km_trace = tr;
+            o.weight = 1.0;
+            return;
+        }
         size_t DD = (size_t)D * D;
         std::vector<double> ar = to_host(a_re, DD, c->stream), ai = a_im ? to_host(a_im, DD, c->stream)
                                                                          : std::vector<double>(DD, 0.0);

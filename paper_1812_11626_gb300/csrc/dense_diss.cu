@@ -19,6 +19,8 @@
 // Kossakowski matrix, N^4 complex for M (built from A through the sparse basis matrix in
 // O(D^2 + N^5) operations).  R is then compressed to CSR without its exact zeros.
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "internal.cuh"
 #include "prim.cuh"
@@ -273,7 +275,105 @@ void dense_R_K(gksl_ctx *c, const Kern<MODE> &kern, CsrR &R, DBuf<double> &K) {
     GK_CUDA(cudaStreamSynchronize(s));
 }
 
+// Kossakowski matrix upload (gksl_set_kossakowski at N > 64): interleave the planar entries into A
+// and flag a non-finite entry (bit 1); the largest |a_jk| goes to *maxbits as the bit pattern of a
+// non-negative double (whose unsigned order is the order of the values), one atomic per warp.
+__global__ void k_km_pack(const double *__restrict__ re, const double *__restrict__ im, long long n,
+                          double2 *__restrict__ A, unsigned long long *__restrict__ maxbits, int *__restrict__ flag) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double m = 0.0;
+    if (i < n) {
+        const double x = re[i], y = im ? im[i] : 0.0;
+        A[i] = make_double2(x, y);
+        if (!isfinite(x) || !isfinite(y)) atomicOr(flag, 1);
+        else m = hypot(x, y);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
+}
+
+// Necessary conditions of positive semidefiniteness and Hermiticity for entry (j, k), k >= j
+// (thread x walks k, so the reads of row j are coalesced): |a_jk - conj(a_kj)| within tol_h
+// (bit 2), a_jj >= -eps (bit 4), |a_jk|^2 <= max(a_jj, 0) max(a_kk, 0) + minor_eps (bit 8).
+__global__ void k_km_check(const double2 *__restrict__ A, long long D, double tol_h, double eps, double minor_eps,
+                           int *__restrict__ flag) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long j = blockIdx.y;
+    if (k >= D || k < j) return;
+    const double2 a = A[j * D + k], b = A[k * D + j];
+    int f = 0;
+    if (fabs(a.x - b.x) > tol_h || fabs(a.y + b.y) > tol_h) f |= 2;
+    const double ajj = A[j * D + j].x;
+    if (k == j) {
+        if (ajj < -eps) f |= 4;
+    } else {
+        const double akk = A[k * D + k].x;
+        if (a.x * a.x + a.y * a.y > fmax(ajj, 0.0) * fmax(akk, 0.0) + minor_eps) f |= 8;
+    }
+    if (f) atomicOr(flag, f);
+}
+
+__global__ void k_km_diag(const double2 *__restrict__ A, long long D, double *__restrict__ d) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < D) d[j] = A[j * D + j].x;
+}
+
 }  // namespace
+
+double kossakowski_upload_checked(gksl_ctx *c, const double *a_re, const double *a_im, DBuf<double2> &A) {
+    NvtxRange nv("Kossakowski matrix: upload and checks");
+    cudaStream_t s = c->stream;
+    const long long D = c->D;
+    const size_t DD = (size_t)D * (size_t)D;
+    // planar device copies of host input (device input is read in place)
+    DBuf<double> dre, dim;
+    const double *re = a_re, *im = a_im;
+    if (!is_device_ptr(a_re)) {
+        dre.alloc(DD);
+        GK_CUDA(cudaMemcpyAsync(dre.p, a_re, sizeof(double) * DD, cudaMemcpyDefault, s));
+        re = dre.p;
+    }
+    if (a_im && !is_device_ptr(a_im)) {
+        dim.alloc(DD);
+        GK_CUDA(cudaMemcpyAsync(dim.p, a_im, sizeof(double) * DD, cudaMemcpyDefault, s));
+        im = dim.p;
+    }
+    A.alloc(DD);
+    DBuf<int> flag(1);
+    DBuf<unsigned long long> maxbits(1);
+    GK_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    GK_CUDA(cudaMemsetAsync(maxbits.p, 0, sizeof(unsigned long long), s));
+    k_km_pack<<<grid_for((long long)DD, kT), kT, 0, s>>>(re, im, (long long)DD, A.p, maxbits.p, flag.p);
+    GK_LAUNCH_CHECK();
+    int hf = 0;
+    unsigned long long hb = 0;
+    GK_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(&hb, maxbits.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    dre.release();
+    dim.release();
+    GK_REQUIRE(!(hf & 1), GKSL_ERR_ARG, "non-finite Kossakowski entry");
+    double mx;
+    std::memcpy(&mx, &hb, sizeof mx);
+    const double eps = 1e-12 * mx;
+    k_km_check<<<dim3((unsigned)((D + kT - 1) / kT), (unsigned)D), kT, 0, s>>>(A.p, D, 1e-12 * mx, eps, eps * mx * 4.0,
+                                                                           flag.p);
+    GK_LAUNCH_CHECK();
+    DBuf<double> dg((size_t)D);
+    k_km_diag<<<grid_for(D, kT), kT, 0, s>>>(A.p, D, dg.p);
+    GK_LAUNCH_CHECK();
+    std::vector<double> hd((size_t)D);
+    GK_CUDA(cudaMemcpyAsync(hd.data(), dg.p, sizeof(double) * D, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    GK_REQUIRE(!(hf & 2), GKSL_ERR_ARG, "Kossakowski matrix is not Hermitian");
+    GK_REQUIRE(!(hf & 4), GKSL_ERR_ARG, "Kossakowski matrix is not positive semidefinite");
+    GK_REQUIRE(!(hf & 8), GKSL_ERR_ARG,
+               "Kossakowski matrix is not positive semidefinite (a 2 x 2 principal minor is negative)");
+    double tr = 0.0;
+    for (long long j = 0; j < D; ++j) tr += hd[(size_t)j];
+    return tr;
+}
 
 void dense_dissipator_channel(gksl_ctx *c, const Op &op, CsrR &R, DBuf<double> &K) {
     NvtxRange nv("dense dissipator (channel)");

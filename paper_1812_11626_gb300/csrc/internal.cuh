@@ -56,6 +56,11 @@ void mf_step(gksl_ctx *c, int precision, double h, const double *tab, long long 
 // ---- dense_diss.cu (dissipators through their matrix-unit form, O(N^4); Eq. 8)
 constexpr int kDenseDissMaxN = 200;   // dense R: D^2 < 2^31 entries
 constexpr int kDenseKmMaxN = 128;     // Kossakowski kernel M: N^4 complex (4.3 GB at N = 128)
+// Copy a D x D Kossakowski matrix (planar re / im, host or device; im may be null) into A
+// (interleaved, device) and check on the device that it is finite, Hermitian to 1e-12 max|a| and
+// passes the diagonal and 2 x 2 minor conditions of positive semidefiniteness; GKSL_ERR_ARG
+// otherwise.  Returns its trace (summed on the host in index order).
+double kossakowski_upload_checked(gksl_ctx *c, const double *a_re, const double *a_im, DBuf<double2> &A);
 // R (unit rate, CSR without exact zeros) and K of one jump operator, any N x N matrix
 void dense_dissipator_channel(gksl_ctx *c, const Op &op, CsrR &R, DBuf<double> &K);
 // R and K of the Eq. 8 dissipator of a D x D Kossakowski matrix (device, row-major)

@@ -243,3 +243,62 @@ def test_dense_routes_reject_sizes_past_their_limits(G):
         assert e.value.status == G.GKSL_ERR_ARG and "N <= 128" in str(e.value)
     finally:
         G.gksl_destroy(ctx)
+
+
+def test_kossakowski_device_checks_at_n65(G):
+    """Above N = 64 a Kossakowski matrix is copied to the device and checked there.  At N = 65
+    (D = 4 224): a non-finite entry, a non-Hermitian pair, a negative diagonal entry and an
+    oversized off-diagonal pair (a negative 2 x 2 principal minor) are each rejected with the host
+    route's status and message, and leave the channel set before them in place (its assembled R
+    equals that of a context holding only that channel, bit for bit); a valid matrix given as host
+    arrays and as CUDA tensors assembles to the same R bit for bit."""
+    import torch
+    N = 65
+    D = N * N - 1
+    re, im = W.random_kossakowski(N, 65, scale=0.1)
+    L = W.random_operator(N, 0.05, 66)
+
+    def assembled_r(ctx, p):
+        G.gksl_set_drive(ctx, 0.0, 0.0, 1.0)
+        G.gksl_assemble(ctx, 0)
+        return _csr(G, ctx, G.GKSL_MAT_R + p)
+
+    ref = G.gksl_create(N)
+    try:
+        G.set_csr_operator(G.gksl_set_dissipator, ref, 1, 0.3, op=L)
+        R_ref = assembled_r(ref, 1)
+    finally:
+        G.gksl_destroy(ref)
+    ctx = G.gksl_create(N)
+    try:
+        G.set_csr_operator(G.gksl_set_dissipator, ctx, 1, 0.3, op=L)
+        cases = []
+        bad = re.copy(); bad[7, 11] = np.nan
+        cases.append((bad, im, "non-finite"))
+        bad = re.copy(); bad[3, 9] += 1e-3 * np.abs(re).max()
+        cases.append((bad, im, "not Hermitian"))
+        bad = re.copy(); bad[D - 1, D - 1] = -1.0
+        cases.append((bad, im, "not positive semidefinite"))
+        bad = re.copy(); bad[1, 2] = bad[2, 1] = 10.0 * np.sqrt(re[1, 1] * re[2, 2])
+        cases.append((bad, im, "2 x 2 principal minor"))
+        for a_re, a_im, what in cases:
+            with pytest.raises(G.GkslError) as e:
+                G.gksl_set_kossakowski(ctx, a_re, a_im)
+            assert e.value.status == G.GKSL_ERR_ARG and what in str(e.value), (what, str(e.value))
+        R_kept = assembled_r(ctx, 1)
+        assert (R_kept != R_ref).nnz == 0
+    finally:
+        G.gksl_destroy(ctx)
+    Rs = []
+    for on_device in (False, True):
+        ctx = G.gksl_create(N)
+        try:
+            if on_device:
+                dev = torch.device("cuda", 0)
+                G.gksl_set_kossakowski(ctx, torch.as_tensor(re, device=dev), torch.as_tensor(im, device=dev))
+            else:
+                G.gksl_set_kossakowski(ctx, re, im)
+            Rs.append(assembled_r(ctx, 0))
+        finally:
+            G.gksl_destroy(ctx)
+    assert Rs[0].nnz > 0 and (Rs[0] != Rs[1]).nnz == 0
