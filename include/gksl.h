@@ -92,7 +92,10 @@ gksl_status gksl_set_dissipator(gksl_ctx *ctx, int p, double gamma_p, const int 
  * channel 0 holds the whole Eq. 8 dissipator at gamma_0 = 1, assembled by the dense route
  * (N <= 128; A, its kernel M and the transient take about 16 (D^2 + 2 N^4) bytes); positive
  * semidefiniteness is then checked through the diagonal and the 2 x 2 principal minors only
- * (a_jj >= 0, |a_jk|^2 <= a_jj a_kk).  GKSL_ERR_ARG if A is not Hermitian or fails those checks. */
+ * (a_jj >= 0, |a_jk|^2 <= a_jj a_kk).  GKSL_ERR_ARG if A is not Hermitian or fails those checks.
+ * a_re and a_im may be host or device memory; above N = 64 A is copied to the device first and
+ * checked there (the same conditions), and a rejected A leaves the previous channels in place.
+ * GKSL_ERR_OOM if the device cannot hold A (plus a planar copy of host input) during the call. */
 gksl_status gksl_set_kossakowski(gksl_ctx *ctx, const double *a_re, const double *a_im, double tol);
 /* Change gamma_p of an existing channel without re-expanding it. */
 gksl_status gksl_set_gamma(gksl_ctx *ctx, int p, double gamma_p);
