@@ -123,11 +123,28 @@ __device__ inline AT ell_dot_full(const HybView<VT> &H, long long r, const VT *_
     return s;
 }
 
+// (C y)_i of long row i by one warp: each lane sums its entries e, e + 32, ... in order, eight of
+// them in flight at a time (the sums are those of a one-at-a-time loop bit for bit), then a warp
+// reduction.  Eight in flight matter where long rows are most of the matrix (a dense L).
 template <typename VT, typename AT>
 __device__ inline AT tail_dot(const HybView<VT> &H, long long i, int lane, const VT *__restrict__ y) {
     AT s = AT(0);
-    int e1 = H.tail_ptr[i + 1];
-    for (int e = H.tail_ptr[i] + lane; e < e1; e += 32) s += (AT)ldcs(H.tail_val + e) * (AT)__ldg(y + H.tail_col[e]);
+    const int e1 = H.tail_ptr[i + 1];
+    int e = H.tail_ptr[i] + lane;
+    for (; e + 224 < e1; e += 256) {
+        int cc[8];
+        VT vv[8], yy[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            cc[u] = H.tail_col[e + 32 * u];
+            vv[u] = ldcs(H.tail_val + e + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) yy[u] = __ldg(y + cc[u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (AT)vv[u] * (AT)yy[u];
+    }
+    for (; e < e1; e += 32) s += (AT)ldcs(H.tail_val + e) * (AT)__ldg(y + H.tail_col[e]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
