@@ -27,6 +27,17 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+bool device_local_ptr(const void *p, int device) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == device);
+}
+
 void copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
     if (bytes == 0) return;
     GK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
@@ -651,7 +662,7 @@ extern "C" gksl_status gksl_observable_diag(gksl_ctx *c, const double *o_diag, c
         copy_in(o.p, o_diag, sizeof(double) * c->N, c->stream);
         const double *vd = v;
         DBuf<double> vtmp;
-        if (!is_device_ptr(v)) {
+        if (!device_local_ptr(v, c->device)) {   // host memory or another GPU's: copy it here first
             vtmp.alloc((size_t)(count * c->D));
             copy_in(vtmp.p, v, sizeof(double) * count * c->D, c->stream);
             vd = vtmp.p;

@@ -325,15 +325,15 @@ double kossakowski_upload_checked(gksl_ctx *c, const double *a_re, const double 
     cudaStream_t s = c->stream;
     const long long D = c->D;
     const size_t DD = (size_t)D * (size_t)D;
-    // planar device copies of host input (device input is read in place)
+    // planar copies of host input and of another GPU's memory (this device's is read in place)
     DBuf<double> dre, dim;
     const double *re = a_re, *im = a_im;
-    if (!is_device_ptr(a_re)) {
+    if (!device_local_ptr(a_re, c->device)) {
         dre.alloc(DD);
         GK_CUDA(cudaMemcpyAsync(dre.p, a_re, sizeof(double) * DD, cudaMemcpyDefault, s));
         re = dre.p;
     }
-    if (a_im && !is_device_ptr(a_im)) {
+    if (a_im && !device_local_ptr(a_im, c->device)) {
         dim.alloc(DD);
         GK_CUDA(cudaMemcpyAsync(dim.p, a_im, sizeof(double) * DD, cudaMemcpyDefault, s));
         im = dim.p;
