@@ -448,9 +448,6 @@ inline unsigned grid_for(long long n, int threads) {
 }
 
 bool is_device_ptr(const void *p);
-// device memory of `device` (or managed memory), which this library's kernels on it may read in
-// place; host memory and other GPUs' memory is copied in first
-bool device_local_ptr(const void *p, int device);
 // copy `bytes` from a host-or-device pointer to device memory on stream s
 void copy_in(void *dst_dev, const void *src, size_t bytes, cudaStream_t s);
 // copy `bytes` from device memory to a host-or-device pointer (synchronises for host targets)

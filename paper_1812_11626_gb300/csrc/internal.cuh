@@ -56,6 +56,9 @@ void mf_step(gksl_ctx *c, int precision, double h, const double *tab, long long 
 // ---- dense_diss.cu (dissipators through their matrix-unit form, O(N^4); Eq. 8)
 constexpr int kDenseDissMaxN = 200;   // dense R: D^2 < 2^31 entries
 constexpr int kDenseKmMaxN = 128;     // Kossakowski kernel M: N^4 complex (4.3 GB at N = 128)
+// device memory of `device` (or managed memory), which this library's kernels on it may read in
+// place; host memory and other GPUs' memory is copied in first
+bool device_local_ptr(const void *p, int device);
 // Copy a D x D Kossakowski matrix (planar re / im, host or device; im may be null) into A
 // (interleaved, device) and check on the device that it is finite, Hermitian to 1e-12 max|a| and
 // passes the diagonal and 2 x 2 minor conditions of positive semidefiniteness; GKSL_ERR_ARG
