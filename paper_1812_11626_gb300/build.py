@@ -14,7 +14,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgksl.so")
 UNITS = ["prim.cu", "expand.cu", "structure.cu", "assemble.cu", "hyb.cu", "rk4.cu", "adjoint.cu", "batch.cu",
-         "api.cu", "noalloc.cu", "mfree.cu", "dense_diss.cu", "rates.cu"]
+         "api.cu", "noalloc.cu", "mfree.cu", "dense_diss.cu", "rates.cu", "rk4_block.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr"]

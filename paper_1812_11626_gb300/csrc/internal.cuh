@@ -29,6 +29,11 @@ void propagate(gksl_ctx *c, long long spp, long long n_steps, int precision, lon
 void ensure_work(gksl_ctx *c, bool fp32);
 void clear_graphs(gksl_ctx *c);
 bool state_finite(gksl_ctx *c);
+// small systems (CSR form; by default up to D + 1 = 256 rows in FP64, 576 in FP32): a chunk of
+// RK4 steps by one thread block with the state in shared memory (rk4_block.cu);
+// GKSL_RK4_BLOCK=0/1 forces it off/on (on: wherever D + 1 <= 4096)
+bool rk4_block_applies(const gksl_ctx *c, int precision);
+void rk4_block_run(gksl_ctx *c, int precision, double h, const double *tab, long long first, long long count);
 // drive table eps(t) - E for steps [0, n) of a run starting at t0
 void fill_eps_table(gksl_ctx *c, double t0, double h, long long n);
 // the square drive's jumps must fall on the step grid (even steps/period, time on the grid)

@@ -664,6 +664,10 @@ cudaGraphExec_t graph_for(gksl_ctx *c, long long steps, int precision, double h,
 }
 
 void run_steps(gksl_ctx *c, int precision, double h, const double *tab, long long first, long long count) {
+    if (rk4_block_applies(c, precision)) {   // a small system: the whole chunk in one launch
+        rk4_block_run(c, precision, h, tab, first, count);
+        return;
+    }
     long long n = first, end = first + count;
     while (end - n >= kGraphSteps) {
         k_set_ll<<<1, 1, 0, c->stream>>>(c->step_base.p, n);

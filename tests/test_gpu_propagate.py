@@ -457,3 +457,57 @@ def test_folded_q1_matches_separate_stream(G):
         assert G.gksl_get_info(ctx).q1_folded == 0
     finally:
         G.gksl_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["dimer6", "dimer10", "dimer24", "dimer64", "dimer10_nofold", "general7"])
+def test_block_path_matches_stage_kernels(G, case, monkeypatch):
+    """Small systems run a whole chunk of RK4 steps in one thread block with the state in shared
+    memory (by default up to D + 1 = 256 rows in FP64 and 576 in FP32; GKSL_RK4_BLOCK=1 forces it
+    wherever D + 1 <= 4096).  Each row is summed as in the stage kernels and updated by the same
+    stage functions, so the states equal the stage kernels' (GKSL_RK4_BLOCK=0) bit for bit: the
+    dimer with 18 ELL slots and Q1 folded (N = 6, 10, 24, and 64, the largest that fits), Q1 kept
+    apart (GKSL_ASM_NO_FOLD), and a general system whose ELL width differs from 18 and whose long
+    rows go to warps; both precisions, with the FP32 form's FP64 correction steps, over 300 steps
+    emitted every 75 (chunks that are not multiples of the stage kernels' 64-step graphs)."""
+    import os
+    if case.startswith("dimer"):
+        N = int(case[5:].split("_")[0])
+        d = W.dimer(N)
+        flags = G.GKSL_ASM_FP32 | (G.GKSL_ASM_NO_FOLD if case.endswith("nofold") else 0)
+        make = lambda: G.dimer_context(d, flags=flags)
+        rho = d.rho0_dense()
+    else:
+        N = 7
+        H = W.random_operator(N, 0.6, 31, hermitian=True)
+        H1 = W.random_operator(N, 0.4, 32, hermitian=True)
+        L = W.random_operator(N, 0.5, 33)
+        re, im = W.random_density_matrix(N, 2, 34)
+        rho = re + 1j * im
+
+        def make():
+            ctx = G.gksl_create(N)
+            G.set_csr_operator(G.gksl_set_h0_component, ctx, 0, 0.8, op=H)
+            G.set_csr_operator(G.gksl_set_h1, ctx, op=H1)
+            G.set_csr_operator(G.gksl_set_dissipator, ctx, 0, 0.1, op=L)
+            G.gksl_set_drive(ctx, 0.2, 0.6, 1.5)
+            G.gksl_assemble(ctx, G.GKSL_ASM_FP32)
+            return ctx
+    D = N * N - 1
+    outs = {}
+    for block in ("0", "1"):
+        monkeypatch.setenv("GKSL_RK4_BLOCK", block)
+        ctx = make()
+        try:
+            spp = G.gksl_min_stable_steps(ctx) * 2
+            info = G.gksl_get_info(ctx)
+            if case == "general7":
+                assert info.ell_width_q0 != 18 and info.long_rows > 0
+            for prec, corr in ((64, 0), (32, 0), (32, 100)):
+                G.gksl_set_rho0(ctx, rho.real.copy(), rho.imag.copy())
+                outs[(block, prec, corr)] = run_gpu(G, ctx, spp, 300, 75, precision=prec, corr=corr, D=D)
+        finally:
+            G.gksl_destroy(ctx)
+    for key in ((64, 0), (32, 0), (32, 100)):
+        a, b = outs[("0",) + key], outs[("1",) + key]
+        assert np.isfinite(a).all() and np.abs(a).max() > 0
+        assert np.array_equal(a, b), (key, np.abs(a - b).max())
