@@ -469,6 +469,7 @@ def main():
         extras["matrix_free"] = matrix_free_extras(G, W, torch, stream, d, spp, args.steps)
         extras.update(batched_and_adjoint(G, W, torch, l2_rate))
         extras.update(dense_and_asymptotic(G, W, torch))
+        extras.update(small_configs(G, W, torch))
         extras["measured_rates"] = {"fp64_fma_per_s": fma_rate, "l2_read_gbs": l2_rate / 1e9,
                                     "how": "gksl_measure_rates: FP64 FMA chains on 4 CTAs per SM checked bit for bit "
                                            "against the host recurrence; 64 passes over a 32 MiB L2-resident buffer "
@@ -753,6 +754,58 @@ def batched_and_adjoint(G, W, torch, l2_rate=None):
         out["adjoint_plain_fp64_steps_per_s"] = S / (time.perf_counter() - t0)
     finally:
         G.gksl_destroy(c)
+    return out
+
+
+def small_configs(G, W, torch):
+    """The small workloads: the N = 10 dimer over its stated 10 periods of 200 steps (v emitted at
+    every period end), through the one-block path the library uses at this size and through the
+    stage kernels (GKSL_RK4_BLOCK=0), FP64; and the N = 100 dimer's FP64 and FP32 rates over 20 000
+    steps at 4 000 steps per period."""
+    import numpy as np
+    out = {}
+    d = W.dimer(10)
+    ctx = G.dimer_context(d)
+    try:
+        D = d.N * d.N - 1
+        v = np.zeros((10, D))
+        res = {}
+        for name, env in (("one block", None), ("stage kernels", "0")):
+            old = os.environ.get("GKSL_RK4_BLOCK")
+            if env is None:
+                os.environ.pop("GKSL_RK4_BLOCK", None)
+            else:
+                os.environ["GKSL_RK4_BLOCK"] = env
+            try:
+                best = 1e9
+                for _ in range(4):
+                    G.gksl_set_rho0(ctx, d.rho0_dense().real.copy())
+                    t0 = time.perf_counter()
+                    G.gksl_propagate(ctx, 200, 2000, 64, 0, 200, v)
+                    best = min(best, time.perf_counter() - t0)
+            finally:
+                if old is None:
+                    os.environ.pop("GKSL_RK4_BLOCK", None)
+                else:
+                    os.environ["GKSL_RK4_BLOCK"] = old
+            res[name] = {"seconds": best, "steps_per_s": 2000 / best}
+        out["config_n10_fp64_10_periods"] = res
+    finally:
+        G.gksl_destroy(ctx)
+    d = W.dimer(100)
+    ctx = G.dimer_context(d)
+    try:
+        res = {}
+        for prec in (64, 32):
+            G.gksl_propagate(ctx, 4000, 4000, prec, 0, 0, None)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G.gksl_propagate(ctx, 4000, 20000, prec, 0, 0, None)
+            torch.cuda.synchronize()
+            res[f"fp{prec}_steps_per_s"] = 20000 / (time.perf_counter() - t0)
+        out["config_n100"] = res
+    finally:
+        G.gksl_destroy(ctx)
     return out
 
 
