@@ -206,7 +206,10 @@ gksl_status gksl_min_stable_steps(gksl_ctx *ctx, long long *steps_per_period);
  * every `correction_every` steps (<= 0: never), one full FP64 step in place of an FP32 one.
  * Every `emit_every` steps (<= 0: never) the FP64 state is copied to v_out, which holds
  * (n_steps / emit_every) rows of D doubles.  Returns GKSL_ERR_DIVERGED if the state is
- * non-finite at an emission point or at the end. */
+ * non-finite at an emission point or at the end.  Small systems (up to D + 1 = 256 rows in FP64,
+ * 576 in FP32) run each stretch of steps between emissions in one thread block with the state in
+ * shared memory, with the same results bit for bit as the per-stage kernels; the environment
+ * variable GKSL_RK4_BLOCK=0 turns that off, =1 uses it wherever D + 1 <= 4096. */
 gksl_status gksl_propagate(gksl_ctx *ctx, long long steps_per_period, long long n_steps, int precision,
                            long long correction_every, long long emit_every, double *v_out);
 
