@@ -279,6 +279,8 @@ def main():
                     help="profiling case for ncu: the N=1000 matrix-free form, 20 FP64 and 20 FP32 RK4 steps")
     ap.add_argument("--profile-adjoint-small", action="store_true",
                     help="profiling case for ncu: the FP64 adjoint at N=200 over one period of 64 steps")
+    ap.add_argument("--profile-block", action="store_true",
+                    help="profiling case for ncu: the N=10 workload, 10 periods of 200 FP64 steps on one block")
     ap.add_argument("--profile-adjoint-small-fp32", action="store_true",
                     help="profiling case for ncu: the same with the FP32 adjoint (its wide reverse stages)")
     ap.add_argument("--profile-dense", action="store_true",
@@ -301,6 +303,9 @@ def main():
         return
     if args.profile_adjoint_small:
         run_profile_adjoint(200)
+        return
+    if args.profile_block:
+        run_profile_block()
         return
     if args.profile_adjoint_small_fp32:
         run_profile_adjoint(200, 32)
@@ -607,6 +612,25 @@ def run_profile_batch():
     G.gksl_batch_destroy(b)
     for c in ctxs:
         G.gksl_destroy(c)
+
+
+def run_profile_block():
+    """Small, fixed case for ncu: the N = 10 dimer over its stated 10 periods of 200 FP64 steps,
+    v emitted at every period end, so the one-block kernel runs 10 launches of 200 steps."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import numpy as np
+    from paper_1812_11626_gb300 import gksl as G
+    from paper_1812_11626_gb300 import workloads as W
+    d = W.dimer(10)
+    ctx = G.dimer_context(d)
+    v = np.zeros((10, d.N * d.N - 1))
+    t0 = time.perf_counter()
+    G.gksl_propagate(ctx, 200, 2000, 64, 0, 200, v)
+    el = time.perf_counter() - t0
+    print(json.dumps({"profile_case": "block N=10", "seconds": el, "v_last_max": float(np.abs(v[-1]).max())}),
+          flush=True)
+    G.gksl_destroy(ctx)
 
 
 def run_profile_adjoint(N=N_BENCH, precision=64):
