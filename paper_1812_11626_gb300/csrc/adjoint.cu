@@ -641,7 +641,10 @@ void adjoint_timeavg(gksl_ctx *c, const double *o_diag, long long S, long long p
     const long long nsteps = period * S, first = (period - 1) * S;
     const double t0 = c->t;
     check_drive_grid(c, S, h);
-    fill_eps_table(c, t0, h, nsteps);
+    fill_eps_table(c, t0, h, std::max(nsteps, 8LL));   // the variant timer below reads 8 steps
+    // the forward passes use the stage-kernel variant the timer picks for this matrix, as
+    // gksl_propagate does (a context used only for gradients would otherwise keep variant 0)
+    tune_stage_variant(c, precision, h);
     DBuf<double> theta((size_t)(3 * nsteps));
     fill_theta_table(c, t0, h, nsteps, theta.p);
 

@@ -36,6 +36,9 @@ bool rk4_block_applies(const gksl_ctx *c, int precision);
 void rk4_block_run(gksl_ctx *c, int precision, double h, const double *tab, long long first, long long count);
 // drive table eps(t) - E for steps [0, n) of a run starting at t0
 void fill_eps_table(gksl_ctx *c, double t0, double h, long long n);
+// time the stage-kernel variants on this context once per precision (as the first gksl_propagate
+// does) with the drive table filled from the current time for at least 8 steps
+void tune_stage_variant(gksl_ctx *c, int precision, double h);
 // the square drive's jumps must fall on the step grid (even steps/period, time on the grid)
 void check_drive_grid(const gksl_ctx *c, long long spp, double h);
 // `count` RK4 steps on the context state starting at global step `first` (drive table index)

@@ -688,6 +688,8 @@ void run_steps(gksl_ctx *c, int precision, double h, const double *tab, long lon
 
 }  // namespace
 
+void tune_stage_variant(gksl_ctx *c, int precision, double h) { tune_variant(c, precision, h, c->eps_tab.p); }
+
 void clear_graphs(gksl_ctx *c) {
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
     c->graphs.clear();
